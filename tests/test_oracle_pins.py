@@ -1,0 +1,334 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test names what fixes the expected value: a closed form, an invariant of the
+discretisation, a number the paper prints, or a brute-force / library computation on
+a tiny grid.  ``test_planted_*`` plant plausible mistakes in a copy of the oracle and
+check that a pin catches each of them.
+"""
+
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import dense, krylov, mac, stokes
+from paper_2307_05266_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _random_mask(shape, phi, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.random(shape) < phi).astype(np.uint8)
+
+
+SMALL_GEOMETRIES = [
+    ((6, 7), 0.75, 1, None),
+    ((5, 6, 4), 0.8, 2, None),
+    ((7, 5), 0.8, 3, (True, False)),
+    ((4, 5, 6), 0.85, 4, (False, True, True)),
+    ((6, 6, 5), 0.7, 5, (True, True, False)),
+]
+
+
+def _load_table(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append([float(v) for v in line.split()])
+    return rows
+
+
+# ---- operator invariants --------------------------------------------------------
+@pytest.mark.parametrize("shape,phi,seed,periodic", SMALL_GEOMETRIES)
+def test_gradient_is_transpose_of_divergence(shape, phi, seed, periodic):
+    """eq. coupled_matrix: the discrete gradient is the adjoint of -div.  B and B^T are
+    assembled from their own definitions, so a sign or index slip in either breaks
+    the identity."""
+    geo = mac.classify(_random_mask(shape, phi, seed), periodic)
+    B = mac.assemble_B(geo)
+    G = mac.assemble_grad(geo)
+    assert abs(G - B.T).max() == 0.0
+    assert B.nnz == 2 * geo.n_u
+
+
+@pytest.mark.parametrize("shape,phi,seed,periodic", SMALL_GEOMETRIES)
+def test_A_symmetric_positive_definite(shape, phi, seed, periodic):
+    """A = -Delta_h with no-slip walls is symmetric, and positive definite once every
+    face component meets a wall."""
+    geo = mac.classify(_random_mask(shape, phi, seed), periodic)
+    A = mac.assemble_A(geo)
+    assert abs(A - A.T).max() == 0.0
+    w = np.linalg.eigvalsh(A.toarray())
+    assert w[0] > 0.0
+
+
+def test_flags_by_hand():
+    """Flag bytes of a 4x4 periodic box with one solid voxel at (x=1, y=2), worked out by
+    hand: bit 0 = both cells fluid, bits 1..3 = solid-solid tangential neighbours."""
+    m = np.ones((4, 4), np.uint8)
+    m[2, 1] = 0
+    flags = mac.face_flags(mac.classify(m))
+    fx, fy = flags[0], flags[1]
+    # x-faces touching the solid voxel are walls: lower face of (1,2) and of (2,2)
+    assert fx[2, 1] == 0 and fx[2, 2] == 0
+    # no two solid voxels are adjacent, so no face is solid-solid and no ghost appears
+    assert np.all((fx >> 1) == 0) and np.all((fy >> 1) == 0)
+    assert fx.sum() == 14 and fy.sum() == 14
+
+
+def test_flags_ghosts_by_hand():
+    """A solid row y = 0 in a 4x4 periodic box: the x-faces of row 1 have the solid-solid
+    x-face of row 0 as their -y neighbour (one ghost), row 3 has it as +y neighbour."""
+    m = np.ones((4, 4), np.uint8)
+    m[0, :] = 0
+    flags = mac.face_flags(mac.classify(m))
+    fx, fy = flags[0], flags[1]
+    assert np.all(fx[0] == 0)
+    assert np.all(fx[1] == 1 | (1 << 1)) and np.all(fx[3] == 1 | (1 << 1))
+    assert np.all(fx[2] == 1)
+    # y-faces: lower face of row 1 and of row 0 are walls, rows 2 and 3 are unknowns
+    assert np.all(fy[0] == 0) and np.all(fy[1] == 0)
+    assert np.all(fy[2] == 1) and np.all(fy[3] == 1)
+
+
+def test_simple_operator_empty_box_symbol():
+    """With no walls diag(A) = 2d/h^2, so S-hat_simple = B B^T h^2 / (2d): the
+    dimensionless periodic Laplacian over 2d, eigenvalues sum_b 4 sin^2(pi k_b / n_b)/(2d)."""
+    shape = (5, 6, 4)                      # [z][y][x]
+    prob = stokes.StokesProblem(np.ones(shape, np.uint8))
+    w = np.sort(np.linalg.eigvalsh(prob.S_simple.toarray()))
+    ks = [np.arange(n) for n in shape]
+    sym = sum(4 * np.sin(np.pi * k / n) ** 2 for k, n in
+              zip(np.meshgrid(*ks, indexing="ij"), shape))
+    np.testing.assert_allclose(w, np.sort((sym / 6.0).ravel()), atol=1e-12)
+
+
+# ---- spectra (Section 1, Section 4.2.4) ----------------------------------------
+@pytest.mark.parametrize("shape", [(6, 6), (5, 7), (4, 4, 4), (3, 4, 5)])
+def test_empty_periodic_box_spectrum_is_unit(shape):
+    """Without no-slip walls S is the identity on mean-free pressures (the paper's
+    conjecture that the non-unit eigenvalues come from the no-slip walls, in the limit
+    with no walls): spectrum {0, 1, ..., 1}."""
+    w = dense.spectrum(stokes.StokesProblem(np.ones(shape, np.uint8)))
+    assert abs(w[0]) < 1e-12
+    np.testing.assert_allclose(w[1:], 1.0, atol=1e-12)
+
+
+@pytest.mark.parametrize("shape,phi,seed,periodic", SMALL_GEOMETRIES)
+def test_lambda_max_is_one(shape, phi, seed, periodic):
+    """lambda_max(S) = 1 (Section 4.2.2, eq. lambda_cg_rate)."""
+    w = dense.spectrum(stokes.StokesProblem(_random_mask(shape, phi, seed), periodic))
+    assert abs(w.max() - 1.0) < 1e-12
+    assert w.min() > -1e-12
+
+
+@pytest.mark.parametrize("N,n_c,n_avg", [(1, 10, 4), (2, 8, 4), (2, 10, 4), (2, 10, 6),
+                                         (3, 8, 4)])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_non_unit_eigenvalue_count_law(N, n_c, n_avg, seed):
+    """eq. spectrum_relation: N_ev = V_surf + 3 N^2 - 1 on square arrays (Section 4.2.4)."""
+    m = synth.square_array_2d(N, n_c, n_avg, 2, seed)
+    w = dense.spectrum(stokes.StokesProblem(m))
+    n_ev = int(np.sum(np.abs(w - 1.0) > 1e-8))
+    assert n_ev == stokes.surface_area(m) + 3 * N * N - 1
+
+
+def test_condition_trend_with_surface_to_volume():
+    """Table 4 / Section 4.2.3: cond(S) grows and cond(S-hat^-1 S) falls as the
+    channels narrow (sigma_s grows)."""
+    cs, cp, sig = [], [], []
+    for n_avg in (4, 6, 8, 10):
+        m = synth.square_array_2d(3, 14, n_avg, 2, seed=7)
+        prob = stokes.StokesProblem(m)
+        cs.append(dense.effective_cond(dense.spectrum(prob)))
+        cp.append(dense.effective_cond(dense.preconditioned_spectrum(prob)))
+        sig.append(stokes.surface_to_volume(m))
+    assert all(np.diff(sig) < 0)
+    assert all(np.diff(cs) < 0), cs
+    assert all(np.diff(cp) > 0), cp
+    assert cs[0] > cp[0] and cs[-1] < cp[-1]
+
+
+# ---- closed-form solutions ------------------------------------------------------
+@pytest.mark.parametrize("precond", [stokes.UZAWA, stokes.SIMPLE])
+def test_plane_poiseuille_permeability(precond):
+    """Discrete plane Poiseuille flow: k = phi (H^2/12 + h^2/6) (golden file)."""
+    for n, m, num, den, _ in _load_table("poiseuille_2d.txt"):
+        n, m = int(n), int(m)
+        mask = synth.channel_2d(n)
+        assert int(mask.sum()) == m * n
+        r = stokes.solve(mask, (1.0, 0.0), stokes.Options(precond=precond, tol=1e-10))
+        assert r["schur"].outer_iters == 0          # g vanishes: x-invariant flow
+        assert abs(r["k"][0] - num / den) <= 1e-12 * (num / den)
+        assert abs(r["k"][1]) <= 1e-15
+
+
+def test_poiseuille_3d_slab():
+    """The same closed form for a 3D slab (walls normal to z, flow along x or y)."""
+    n = 8
+    mask = np.ones((n, n, n), np.uint8)
+    mask[0] = 0
+    mask[n - 1] = 0
+    h, H, phi = 1.0 / n, (n - 2) / n, (n - 2) / n
+    k_exact = phi * (H * H / 12 + h * h / 6)
+    for f, a in (((1.0, 0, 0), 0), ((0, 1.0, 0), 1)):
+        r = stokes.solve(mask, f, stokes.Options(precond=stokes.SIMPLE))
+        assert abs(r["k"][a] - k_exact) <= 1e-12 * k_exact
+
+
+def test_poiseuille_approaches_continuum():
+    """As h -> 0 the discrete channel permeability tends to phi H^2 / 12."""
+    errs = []
+    for n in (8, 16, 32):
+        r = stokes.solve(synth.channel_2d(n), (1.0, 0.0), stokes.Options())
+        H = (n - 2) / n
+        errs.append(abs(r["k"][0] - (n - 2) / n * H * H / 12))
+    assert errs[1] < errs[0] / 3 and errs[2] < errs[1] / 3
+
+
+@pytest.mark.parametrize("precond", [stokes.UZAWA, stokes.SIMPLE])
+def test_channel_cross_force_hydrostatic(precond):
+    """Force across the band: the exact solution is u = 0 with B^T p = f (pressure
+    linear in y inside the band), so the whole Schur path runs with ||g|| != 0."""
+    mask = synth.channel_2d(16)
+    r = stokes.solve(mask, (0.0, 1.0), stokes.Options(precond=precond, tol=1e-8))
+    prob = r["problem"]
+    assert r["schur"].status == krylov.OK and r["schur"].outer_iters >= 1
+    assert np.abs(r["u"]).max() < 1e-9
+    f = mac.force(prob.geo, (0.0, 1.0))
+    # the outer tolerance bounds the residual; the error may be cond(S) times larger
+    np.testing.assert_allclose(prob.BT @ r["p"], f, atol=1e-5)
+
+
+# ---- brute force on tiny grids ---------------------------------------------------
+@pytest.mark.parametrize("shape,phi,seed,periodic", SMALL_GEOMETRIES)
+@pytest.mark.parametrize("precond", [stokes.UZAWA, stokes.SIMPLE])
+def test_cg_solution_equals_dense_min_norm(shape, phi, seed, periodic, precond):
+    """Algorithm 1 with tight inner solves reaches the minimum-norm solution of the
+    dense S p = g; velocity and permeability follow from eq. velocity_schur."""
+    mask = _random_mask(shape, phi, seed)
+    d = len(shape)
+    f = (1.0,) + (0.0,) * (d - 1)
+    r = stokes.solve(mask, f, stokes.Options(precond=precond, tol=1e-11,
+                                             max_outer=500), periodic)
+    prob = r["problem"]
+    S = dense.schur_dense(prob)
+    A = prob.A.toarray()
+    u_f = np.linalg.solve(A, mac.force(prob.geo, f))
+    g = prob.B @ u_f
+    p_ref = dense.min_norm_solution(S, g)
+    u_ref = np.linalg.solve(A, mac.force(prob.geo, f) - prob.BT @ p_ref)
+    # p is unique up to the nullspace of B^T: compare gradients, velocities, k
+    np.testing.assert_allclose(prob.BT @ r["p"], prob.BT @ p_ref, atol=1e-8)
+    np.testing.assert_allclose(r["u"], u_ref, atol=1e-10 * max(1.0, np.abs(u_ref).max()))
+    ux = u_ref[prob.geo.uidx[0][prob.geo.unknown[0]]]
+    k_ref = ux.sum() / mask.size
+    # h^2 |f| is the velocity scale of a one-voxel pore; k is ~0 when x is blocked
+    assert abs(r["k"][0] - k_ref) <= 1e-9 * (abs(k_ref) + prob.geo.h ** 2)
+
+
+def test_inner_pcg_matches_sparse_direct():
+    """Jacobi PCG on A reaches the sparse direct solution."""
+    m = synth.sphere_packing(16, 2, 4, 0.5, seed=3)
+    prob = stokes.StokesProblem(m)
+    b = mac.force(prob.geo, (0.3, -1.0, 0.5))
+    res = prob.solve_A(b, 1e-13, 5000)
+    x = spla.spsolve(prob.A.tocsc(), b)
+    assert res.status == krylov.OK
+    np.testing.assert_allclose(res.x, x, rtol=0, atol=1e-10 * np.abs(x).max())
+
+
+def test_pcg_finite_termination():
+    """CG on an SPD matrix with k distinct eigenvalues converges in k steps."""
+    rng = np.random.default_rng(0)
+    Q, _ = np.linalg.qr(rng.standard_normal((40, 40)))
+    lam = np.repeat([1.0, 2.0, 5.0, 9.0, 30.0], 8)
+    M = (Q * lam) @ Q.T
+    res = krylov.pcg(lambda v: M @ v, rng.standard_normal(40), np.ones(40), 1e-10, 100)
+    assert res.status == krylov.OK and res.iters == 5
+
+
+def test_recovered_velocity_divergence_free():
+    """A u = f - B^T p with S p = g makes B u = 0 up to the solver tolerances."""
+    m = synth.sphere_packing(16, 3, 5, 0.45, seed=1)
+    r = stokes.solve(m, (0.0, 0.0, 1.0), stokes.Options(precond=stokes.SIMPLE, tol=1e-10))
+    prob = r["problem"]
+    div = prob.B @ r["u"]
+    assert np.linalg.norm(div) <= 1e-8 * np.linalg.norm(abs(prob.B) @ np.abs(r["u"]))
+
+
+def test_both_preconditioners_agree():
+    m = synth.sphere_packing(16, 3, 5, 0.4, seed=4)
+    ks = [stokes.solve(m, (1.0, 0, 0), stokes.Options(precond=p, tol=1e-10))["k"][0]
+          for p in (stokes.UZAWA, stokes.SIMPLE)]
+    assert abs(ks[0] - ks[1]) <= 1e-8 * abs(ks[0])
+
+
+# ---- geometry statistics against Table 3 ----------------------------------------
+def test_table3_square_array_statistics():
+    """Table 3: V^f, porosity and sigma_s of the N=7, n_c=50, n_min=2 square arrays, to
+    the paper's print rounding (its last digit may be off by one)."""
+    for n_avg, vf_k, phi_pct, sig_pct in _load_table("table3_square_arrays.txt"):
+        for seed in (0, 1):
+            m = synth.square_array_2d(7, 50, int(n_avg), 2, seed)
+            assert m.shape == (350, 350)
+            assert abs(m.sum() / 1000.0 - vf_k) <= 0.1 + 1e-9
+            assert abs(100 * stokes.porosity(m) - phi_pct) <= 0.1 + 1e-9
+            assert abs(100 * stokes.surface_to_volume(m) - sig_pct) <= 0.1 + 1e-9
+
+
+# ---- planted mistakes: each must fail a pin ------------------------------------
+def _poiseuille_k():
+    r = stokes.solve(synth.channel_2d(16), (1.0, 0.0), stokes.Options())
+    return r["k"][0]
+
+
+def test_planted_dropped_ghost_term(monkeypatch):
+    """Dropping the ghost contribution (diag 2d instead of 2d + g) misses Poiseuille."""
+    orig = mac.classify
+
+    def no_ghosts(mask, periodic=None):
+        geo = orig(mask, periodic)
+        geo.ghosts = [np.zeros_like(g) for g in geo.ghosts]
+        return geo
+
+    monkeypatch.setattr(mac, "classify", no_ghosts)
+    k = _poiseuille_k()
+    assert abs(k - 231 / 4096) > 1e-3 * 231 / 4096
+
+
+def test_planted_gradient_sign(monkeypatch):
+    """A gradient with the wrong sign breaks B^T = transpose(B)."""
+    orig = mac.assemble_grad
+    monkeypatch.setattr(mac, "assemble_grad", lambda geo: -orig(geo))
+    geo = mac.classify(_random_mask((6, 7), 0.75, 1))
+    assert abs(mac.assemble_grad(geo) - mac.assemble_B(geo).T).max() > 0
+
+
+def test_planted_alg1_printed_sign():
+    """Algorithm 1 as printed (r = S p - g, p += alpha d, r += alpha q) does not solve
+    S p = g; the sign-fixed loop does (checked on a dense SPD system)."""
+    rng = np.random.default_rng(1)
+    Q, _ = np.linalg.qr(rng.standard_normal((20, 20)))
+    S = (Q * np.linspace(0.1, 1.0, 20)) @ Q.T
+    g = rng.standard_normal(20)
+    good = krylov.schur_pcg(lambda d: (S @ d, 0), g, lambda r: (r.copy(), 0), 1e-12, 200)
+    assert np.linalg.norm(S @ good.p - g) < 1e-10 * np.linalg.norm(g)
+    # printed variant
+    p = np.zeros(20)
+    r = S @ p - g
+    z = r.copy()
+    d = z.copy()
+    for _ in range(40):
+        q = S @ d
+        alpha = (r @ z) / (d @ q)
+        p = p + alpha * d
+        r_new = r + alpha * q
+        beta = (r_new @ r_new) / (r @ r)
+        d = r_new + beta * d
+        r = z = r_new
+    assert np.linalg.norm(S @ p - g) > 1e-3 * np.linalg.norm(g)
