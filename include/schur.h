@@ -1,0 +1,179 @@
+/*
+ * schur.h - C ABI of the GB300 Pressure Schur Complement Stokes solver.
+ *
+ * The method (Pimanov, Iliev, Oseledets, Muravleva, "On the efficient preconditioning
+ * of the Stokes equations in tight geometries"):
+ *   - a binary voxel image (Section 2.1, eqs. cube_domain, domains_partition) defines
+ *     the fluid region; the no-slip wall is the fluid/solid interface (eq.
+ *     interior_boundary, eq. stokes_bc_noslip); the exterior box is periodic along
+ *     the flagged axes (Section 2.2) and solid along the others;
+ *   - the MAC discretisation gives the block system of eq. coupled_matrix with the
+ *     no-slip vector Laplacian A and the negative divergence B;
+ *   - the pressure solves S p = g with S = B A^-1 B^T, g = B A^-1 f (eqs. schur_system,
+ *     schur_rhs) by the preconditioned CG of Algorithm 1, preconditioned by Uzawa
+ *     (S-hat = I) or diffusive SIMPLE (S-hat = B diag(A)^-1 B^T), eq. schur_uzawa_prec;
+ *   - the velocity follows from A u = f - B^T p (eq. velocity_schur) and the
+ *     permeability from Darcy's law (eq. darcy_law) as the box average of u.
+ *
+ * Conventions shared by every entry point
+ *   mask      uint8, C order [z][y][x] (x fastest), 1 = fluid, 0 = solid.
+ *   dims      dims[0] = n_x, dims[1] = n_y, dims[2] = n_z (ignored when ndim == 2);
+ *             every used extent must be >= 2.
+ *   h         voxel size 1 / n_x (unit box length along x, Section 2.3).
+ *   faces     face (a, c) is the lower face of cell c along axis a (between cells
+ *             c - e_a and c).  Face-space device buffers are laid out [a][stride]
+ *             with element (a, c) at a * stride + c; stride is reported by
+ *             schur_geometry_info (the cell count rounded up to 64).  Cell-space
+ *             buffers hold n_x * n_y * n_z elements in C order.
+ *   flags     one byte per face: bit 0 = unknown (both cells fluid), bits 1..3 =
+ *             number of solid-solid tangential neighbour faces (ghost walls); 0 on
+ *             faces that are not unknowns.
+ *   streams   every call runs on the stream given at creation and is stream-ordered;
+ *             calls that return values to the host synchronise that stream.
+ *   errors    every int-returning call returns 0 (SCHUR_OK) or a SCHUR_E* code and
+ *             leaves a message for schur_last_error() (thread-local).  A handle whose
+ *             call failed with SCHUR_ECUDA should be destroyed.
+ *   threads   one handle must not be used by two host threads at once.
+ */
+#ifndef SCHUR_H
+#define SCHUR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SCHUR_OK          0
+#define SCHUR_EINVAL      1   /* bad argument (dims, ndim, mask values, axis, null pointer) */
+#define SCHUR_ENOMEM      2   /* device allocation failed */
+#define SCHUR_ENOTCONV    3   /* an iteration cap was hit; the last iterate is kept */
+#define SCHUR_EBREAKDOWN  4   /* CG breakdown: d^T q <= 0 or not finite */
+#define SCHUR_ECUDA       5   /* a CUDA runtime call failed */
+#define SCHUR_ESTATE      6   /* call out of order (e.g. recover before solve) */
+
+enum { SCHUR_UZAWA = 0, SCHUR_SIMPLE = 1 };
+enum { SCHUR_STOP_UNPRECOND = 0, SCHUR_STOP_PRECOND = 1 };
+enum { SCHUR_FP64 = 0, SCHUR_MIXED = 1 };
+enum { SCHUR_LOOP_GRAPH = 0, SCHUR_LOOP_HOST = 1 };
+enum { SCHUR_FIELD_P = 0, SCHUR_FIELD_U = 1, SCHUR_FIELD_FLAGS = 2, SCHUR_FIELD_MASK = 3,
+       SCHUR_FIELD_G = 4 };
+enum { SCHUR_DTYPE_U8 = 0, SCHUR_DTYPE_F32 = 1, SCHUR_DTYPE_F64 = 2 };
+
+typedef struct schur_geom* schur_geom_t;
+
+/* Solver options.  Defaults (schur_opts_default): SIMPLE, unpreconditioned stop,
+ * FP64, graph loop, tol 1e-8, tol_inner_A = tol_inner_S = 1e-12, max_outer 2000,
+ * max_inner 20000. */
+typedef struct {
+    int precond;        /* SCHUR_UZAWA | SCHUR_SIMPLE (eq. schur_uzawa_prec)                */
+    int stop_norm;      /* SCHUR_STOP_UNPRECOND: ||r_k||/||r_0|| < tol (Section 4.2.2);
+                           SCHUR_STOP_PRECOND: ||z_k||/||z_0|| < tol (Algorithm 1)          */
+    int precision;      /* SCHUR_FP64 (SCHUR_MIXED is reserved: returns SCHUR_EINVAL)      */
+    int loop_mode;      /* SCHUR_LOOP_GRAPH: one CUDA graph with device-side while loops;
+                           SCHUR_LOOP_HOST: the host drives every loop (debugging)         */
+    int max_outer;      /* cap on outer iterations (S applications)                         */
+    int max_inner;      /* cap on iterations of each inner solve                            */
+    double tol;         /* outer relative tolerance eps_S                                   */
+    double tol_inner_A; /* inner tolerance eps_A: ||M^-1 r||/||M^-1 r_0|| (Section 3.2)     */
+    double tol_inner_S; /* inner tolerance eps_S-hat for the SIMPLE solve (Section 3.2)     */
+} schur_opts;
+
+typedef struct {
+    int status;                  /* SCHUR_OK, SCHUR_ENOTCONV or SCHUR_EBREAKDOWN          */
+    int outer_iters;             /* S applications in Algorithm 1                          */
+    int zero_rhs;                /* 1 when g vanished to rounding and p = 0 was returned   */
+    int inner_status;            /* worst status of the inner solves                       */
+    long long inner_iters_A;     /* all inner A iterations of the call                     */
+    long long inner_iters_S;     /* all inner SIMPLE iterations of the call                */
+    double rel_res;              /* ||r_k|| / ||r_0|| at exit                              */
+    double rel_res_precond;      /* ||z_k|| / ||z_0|| at exit (NaN when not formed)        */
+    double g_norm;               /* ||g||_2                                                */
+    long long kernel_launches;   /* kernels this call ran on the GPU                       */
+} schur_stats;
+
+typedef struct {
+    int ndim;
+    int64_t dims[3];
+    int periodic[3];
+    int64_t n_cells;             /* n_x n_y n_z                                            */
+    int64_t face_stride;         /* stride of face-space buffers (elements)                */
+    int64_t n_unknown[3];        /* unknown faces per axis                                 */
+    int64_t n_fluid;             /* fluid cells                                            */
+    double h;                    /* voxel size 1/n_x                                       */
+    int64_t device_bytes;        /* device memory held by the handle                       */
+} schur_geom_info;
+
+/* Fill *o with the defaults listed above. */
+void schur_opts_default(schur_opts* o);
+
+/* Build a geometry: copies the mask (host or device pointer, detected), builds the face
+ * flags on the GPU and allocates all solver state.  ndim is 2 or 3; periodic[a] != 0
+ * makes axis a periodic (Section 2.2), otherwise the exterior is solid.  stream is a
+ * cudaStream_t (NULL = legacy default stream).  Errors: SCHUR_EINVAL (ndim, dims < 2,
+ * mask value not 0/1), SCHUR_ENOMEM, SCHUR_ECUDA.  The handle owns its device memory. */
+int schur_create_geometry(const uint8_t* mask, int ndim, const int64_t dims[3],
+                          const int periodic[3], void* stream, schur_geom_t* out);
+
+/* Uniform body force f (f[2] ignored in 2D).  Section 2.3: a pressure drop dp over the
+ * unit box along axis a is the force f = dp e_a; the default is f = e_x. */
+int schur_set_force(schur_geom_t g, const double f[3]);
+
+/* Solve S p = g (eqs. schur_system, schur_rhs) by Algorithm 1 from p_0 = 0.  The
+ * residual sign follows standard PCG (r = g - S p).  A right-hand side that vanishes to
+ * rounding (||g|| <= 1e-12 || |B| |A^-1 f| ||) returns p = 0 after 0 iterations.
+ * stats may be NULL.  Returns SCHUR_OK, SCHUR_ENOTCONV, SCHUR_EBREAKDOWN (the iterate
+ * is kept), or SCHUR_EINVAL / SCHUR_ECUDA. */
+int schur_solve(schur_geom_t g, const schur_opts* opts, schur_stats* stats);
+
+/* Velocity recovery A u = f - B^T p (eq. velocity_schur) with the options of the last
+ * schur_solve.  SCHUR_ESTATE before any solve. */
+int schur_recover_velocity(schur_geom_t g, schur_stats* stats);
+
+/* Darcy permeability along axis a (eq. darcy_law, mu = 1, L = 1): the sum of the
+ * recovered u_a over the unknown faces divided by the number of voxels, accumulated in
+ * FP64.  Synchronises the stream.  SCHUR_ESTATE before any recovery. */
+int schur_permeability(schur_geom_t g, int axis, double* k_out);
+
+/* Borrowed device pointer to a field (valid until the next solve/recover or destroy):
+ * P (f64, cells), U (f64, faces), FLAGS (u8, faces), MASK (u8, cells), G (f64, cells). */
+int schur_get_field(schur_geom_t g, int which, void** dev_ptr, int64_t* elems, int* dtype);
+
+int schur_geometry_info(schur_geom_t g, schur_geom_info* info);
+
+/* ---- single operators on caller-owned device buffers (FP64) --------------------------
+ * Inputs are read only on unknown faces / fluid cells (other entries are ignored);
+ * outputs are written everywhere (0 off the unknowns / fluid cells).  Buffers must not
+ * overlap.  These run on the handle's stream and do not synchronise. */
+
+/* y = A x: the no-slip vector Laplacian, h^-2 ((2d + g_f) x_f - sum of unknown
+ * neighbours) on unknown faces (eq. coupled_matrix, MAC scheme of Section 2.1). */
+int schur_apply_A(schur_geom_t g, const double* x, double* y);
+/* p = B u = -div_h u on fluid cells. */
+int schur_apply_B(schur_geom_t g, const double* u, double* p);
+/* u = B^T p = grad_h p on unknown faces. */
+int schur_apply_BT(schur_geom_t g, const double* p, double* u);
+/* q = S-hat_simple p = B diag(A)^-1 B^T p (eq. schur_uzawa_prec) on fluid cells. */
+int schur_apply_simple(schur_geom_t g, const double* p, double* q);
+/* x = A^-1 b by Jacobi PCG from 0 with the relative preconditioned residual stop of
+ * Section 3.2; *iters (may be NULL) gets the iteration count.  Synchronises. */
+int schur_solve_A(schur_geom_t g, const double* b, double* x, double tol, int max_iter,
+                  int* iters);
+
+/* Profiling hook: one launch of a hot solver kernel on the handle's stream, bracketed by
+ * two CUDA events; *ms receives the elapsed time.  kernel: 0 inner-A direction update,
+ * 1 inner-A stencil A p (with p.q), 2 inner-A x/r update (with r.z, z.z), 3-5 the same
+ * three for the SIMPLE operator.  The kernel works on the solver's own buffers (their
+ * contents after the last call); results of later calls are unaffected.  Synchronises. */
+int schur_time_kernel(schur_geom_t g, int kernel, float* ms);
+
+/* Release the handle and all its device memory (NULL is ignored). */
+void schur_destroy(schur_geom_t g);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* schur_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCHUR_H */

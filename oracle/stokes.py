@@ -50,18 +50,31 @@ class StokesProblem:
         # S-hat_simple = B diag(A)^-1 B^T (eq. schur_uzawa_prec), a sparse product
         self.S_simple = (self.B @ (self.BT.multiply(1.0 / self.dA[:, None]))).tocsr()
         self.dS = self.S_simple.diagonal()
+        self.n_comp, self.comp = fluid_components(self.geo)
+        self.comp_size = np.bincount(self.comp, minlength=self.n_comp).astype(np.float64)
 
     # ---- single operators -------------------------------------------------------
     def solve_A(self, v, tol, max_iter):
         return krylov.pcg(lambda x: self.A @ x, v, 1.0 / self.dA, tol, max_iter)
 
     def remove_mean(self, p):
-        return p - p.mean() if p.size else p
+        """Subtract from p its mean on every connected fluid component: the projection
+        onto the range of S-hat_simple (and of S), whose nullspace holds the constants
+        of each component (Section 3.1, Remark on the constant nullspace)."""
+        if not p.size:
+            return p
+        mean = np.bincount(self.comp, weights=p, minlength=self.n_comp) / self.comp_size
+        return p - mean[self.comp]
 
     def solve_simple(self, r, tol, max_iter):
+        """z = S-hat_simple^+ r.  The "special care" of Section 3.2 for the singular
+        pressure operator, read as: the right-hand side is projected onto the range first
+        (rounding leaves it a component along the constants that grows relative to r as
+        the outer residual shrinks, and CG on an inconsistent system does not converge),
+        and the returned solution is projected as well."""
         minv = np.where(self.dS > 0, 1.0 / np.where(self.dS > 0, self.dS, 1.0), 0.0)
-        return krylov.pcg(lambda x: self.S_simple @ x, r, minv, tol, max_iter,
-                          project=self.remove_mean)
+        return krylov.pcg(lambda x: self.S_simple @ x, self.remove_mean(r), minv, tol,
+                          max_iter, project=self.remove_mean)
 
     def apply_S(self, d, tol_A, max_inner):
         res = self.solve_A(self.BT @ d, tol_A, max_inner)
@@ -97,6 +110,7 @@ class StokesProblem:
                 return r.copy(), 0
         else:
             def precond(r):
+                r[:] = self.remove_mean(r)      # the outer residual is projected in place
                 res = self.solve_simple(r, opts.tol_inner_S, opts.max_inner)
                 return res.x, res.iters
 
@@ -123,6 +137,22 @@ def solve(mask, f, opts: Options = None, periodic=None):
     rec = prob.recover_velocity(f, out.p, opts)
     k = [prob.permeability(rec.x, a) for a in range(prob.geo.d)]
     return dict(problem=prob, p=out.p, u=rec.x, g=g, k=k, schur=out, recovery=rec)
+
+
+def fluid_components(geo):
+    """Connected components of the fluid cells, two cells being connected when the face
+    between them is an unknown (periodic axes wrap).  Returns (count, label per fluid
+    cell in pidx order); labels are numbered by the smallest cell index they contain."""
+    from scipy.sparse.csgraph import connected_components
+    G = mac.assemble_grad(geo)              # one row per unknown face: its two cells
+    adj = (abs(G).T @ abs(G)).tocsr()
+    n, lab = connected_components(adj, directed=False)
+    first = np.full(n, geo.n_p, dtype=np.int64)
+    np.minimum.at(first, lab, np.arange(geo.n_p))
+    order = np.argsort(first, kind="stable")
+    rank = np.empty(n, dtype=np.int64)
+    rank[order] = np.arange(n)
+    return n, rank[lab]
 
 
 # ---- geometry statistics (Section 4.1.1) -----------------------------------------

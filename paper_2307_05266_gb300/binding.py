@@ -1,0 +1,270 @@
+"""Thin ctypes binding of ``libschur.so`` (see include/schur.h).
+
+Marshalling only: every step of the solve runs in the CUDA library.  Device buffers are
+passed as raw pointers taken from PyTorch CUDA tensors (PyTorch supplies device memory
+and the stream); host masks are passed as numpy pointers.  There is no CPU fallback:
+``load()`` raises when the library is missing.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+SCHUR_OK, SCHUR_EINVAL, SCHUR_ENOMEM, SCHUR_ENOTCONV = 0, 1, 2, 3
+SCHUR_EBREAKDOWN, SCHUR_ECUDA, SCHUR_ESTATE = 4, 5, 6
+UZAWA, SIMPLE = 0, 1
+STOP_UNPRECOND, STOP_PRECOND = 0, 1
+FP64, MIXED = 0, 1
+LOOP_GRAPH, LOOP_HOST = 0, 1
+FIELD_P, FIELD_U, FIELD_FLAGS, FIELD_MASK, FIELD_G = 0, 1, 2, 3, 4
+
+EXPORTED = [
+    "schur_opts_default", "schur_create_geometry", "schur_set_force", "schur_solve",
+    "schur_recover_velocity", "schur_permeability", "schur_get_field",
+    "schur_geometry_info", "schur_apply_A", "schur_apply_B", "schur_apply_BT",
+    "schur_apply_simple", "schur_solve_A", "schur_time_kernel", "schur_destroy",
+    "schur_last_error",
+]
+KERNELS = {"cgA_dir": 0, "cgA_matvec": 1, "cgA_update": 2, "cgS_dir": 3, "cgS_matvec": 4,
+           "cgS_update": 5}
+
+
+class Opts(C.Structure):
+    _fields_ = [("precond", C.c_int), ("stop_norm", C.c_int), ("precision", C.c_int),
+                ("loop_mode", C.c_int), ("max_outer", C.c_int), ("max_inner", C.c_int),
+                ("tol", C.c_double), ("tol_inner_A", C.c_double), ("tol_inner_S", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("status", C.c_int), ("outer_iters", C.c_int), ("zero_rhs", C.c_int),
+                ("inner_status", C.c_int), ("inner_iters_A", C.c_longlong),
+                ("inner_iters_S", C.c_longlong), ("rel_res", C.c_double),
+                ("rel_res_precond", C.c_double), ("g_norm", C.c_double),
+                ("kernel_launches", C.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class GeomInfo(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("dims", C.c_int64 * 3), ("periodic", C.c_int * 3),
+                ("n_cells", C.c_int64), ("face_stride", C.c_int64),
+                ("n_unknown", C.c_int64 * 3), ("n_fluid", C.c_int64), ("h", C.c_double),
+                ("device_bytes", C.c_int64)]
+
+
+_LIB = None
+
+
+def load(build_if_missing: bool = True):
+    """Load the library (building it in-tree first when it is absent)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.lib_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libschur.so not built at {path}")
+        _build.build()
+    lib = C.CDLL(path)
+    vp, i64p = C.c_void_p, C.POINTER(C.c_int64)
+    sig = {
+        "schur_opts_default": (None, [C.POINTER(Opts)]),
+        "schur_create_geometry": (C.c_int, [vp, C.c_int, i64p, C.POINTER(C.c_int), vp,
+                                            C.POINTER(vp)]),
+        "schur_set_force": (C.c_int, [vp, C.POINTER(C.c_double)]),
+        "schur_solve": (C.c_int, [vp, C.POINTER(Opts), C.POINTER(Stats)]),
+        "schur_recover_velocity": (C.c_int, [vp, C.POINTER(Stats)]),
+        "schur_permeability": (C.c_int, [vp, C.c_int, C.POINTER(C.c_double)]),
+        "schur_get_field": (C.c_int, [vp, C.c_int, C.POINTER(vp), i64p, C.POINTER(C.c_int)]),
+        "schur_geometry_info": (C.c_int, [vp, C.POINTER(GeomInfo)]),
+        "schur_apply_A": (C.c_int, [vp, vp, vp]),
+        "schur_apply_B": (C.c_int, [vp, vp, vp]),
+        "schur_apply_BT": (C.c_int, [vp, vp, vp]),
+        "schur_apply_simple": (C.c_int, [vp, vp, vp]),
+        "schur_solve_A": (C.c_int, [vp, vp, vp, C.c_double, C.c_int, C.POINTER(C.c_int)]),
+        "schur_time_kernel": (C.c_int, [vp, C.c_int, C.POINTER(C.c_float)]),
+        "schur_destroy": (None, [vp]),
+        "schur_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+class SchurError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"schur error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc, allow=(SCHUR_OK,)):
+    if rc not in allow:
+        raise SchurError(rc, load().schur_last_error().decode())
+    return rc
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    load().schur_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    """Raw device pointer of a contiguous CUDA tensor."""
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class _CudaArray:
+    """Zero-copy view of a library-owned device buffer (CUDA array interface)."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None, "stream": None}
+
+
+class Geometry:
+    """Owner of one ``schur_geom_t``: mask -> flags -> solve -> velocity -> permeability.
+
+    ``mask`` is a numpy uint8 array (host) or a CUDA uint8 tensor (device), C order
+    ``[z][y][x]`` or ``[y][x]``.  ``periodic`` lists one flag per physical axis (x, y, z).
+    """
+
+    def __init__(self, mask, periodic=None, stream=None):
+        lib = load()
+        shape = tuple(int(s) for s in mask.shape)
+        ndim = len(shape)
+        if ndim not in (2, 3):
+            raise ValueError("mask must be 2D or 3D")
+        dims = (C.c_int64 * 3)(*(list(reversed(shape)) + [1] * (3 - ndim)))
+        per = periodic if periodic is not None else (True,) * ndim
+        per_c = (C.c_int * 3)(*([int(bool(p)) for p in per] + [1] * (3 - len(per))))
+        if isinstance(mask, np.ndarray):
+            self._host_mask = np.ascontiguousarray(mask, dtype=np.uint8)
+            mptr = self._host_mask.ctypes.data_as(C.c_void_p)
+        else:
+            if mask.dtype.itemsize != 1:
+                raise ValueError("mask tensor must be uint8")
+            self._dev_mask = mask.contiguous()
+            mptr = _ptr(self._dev_mask)
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:          # no torch: legacy default stream
+                stream = 0
+        self.stream = stream
+        h = C.c_void_p()
+        _check(lib.schur_create_geometry(mptr, ndim, dims, per_c, C.c_void_p(stream),
+                                         C.byref(h)))
+        self._h = h
+        self.shape = shape
+        self.ndim = ndim
+        self.info = self.geometry_info()
+
+    # ---- lifetime ----
+    def close(self):
+        if getattr(self, "_h", None):
+            load().schur_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- calls ----
+    def geometry_info(self):
+        gi = GeomInfo()
+        _check(load().schur_geometry_info(self._h, C.byref(gi)))
+        return gi
+
+    def set_force(self, f):
+        f3 = (C.c_double * 3)(*(list(f) + [0.0] * (3 - len(f))))
+        _check(load().schur_set_force(self._h, f3))
+
+    def solve(self, opts=None, allow_fail=False, **kw):
+        o = opts if opts is not None else default_opts(**kw)
+        st = Stats()
+        rc = load().schur_solve(self._h, C.byref(o), C.byref(st))
+        _check(rc, (SCHUR_OK, SCHUR_ENOTCONV, SCHUR_EBREAKDOWN) if allow_fail else (SCHUR_OK,))
+        return st
+
+    def recover_velocity(self, allow_fail=False):
+        st = Stats()
+        rc = load().schur_recover_velocity(self._h, C.byref(st))
+        _check(rc, (SCHUR_OK, SCHUR_ENOTCONV, SCHUR_EBREAKDOWN) if allow_fail else (SCHUR_OK,))
+        return st
+
+    def permeability(self, axis: int) -> float:
+        k = C.c_double()
+        _check(load().schur_permeability(self._h, axis, C.byref(k)))
+        return k.value
+
+    def field(self, which):
+        """Borrowed zero-copy torch view of a library field (valid until the next call)."""
+        import torch
+        p, n, dt = C.c_void_p(), C.c_int64(), C.c_int()
+        _check(load().schur_get_field(self._h, which, C.byref(p), C.byref(n), C.byref(dt)))
+        typestr = {0: "|u1", 1: "<f4", 2: "<f8"}[dt.value]
+        return torch.as_tensor(_CudaArray(p.value, n.value, typestr), device="cuda")
+
+    # ---- single operators on torch CUDA float64 buffers ----
+    def apply_A(self, x, y):
+        _check(load().schur_apply_A(self._h, _ptr(x), _ptr(y)))
+
+    def apply_B(self, u, p):
+        _check(load().schur_apply_B(self._h, _ptr(u), _ptr(p)))
+
+    def apply_BT(self, p, u):
+        _check(load().schur_apply_BT(self._h, _ptr(p), _ptr(u)))
+
+    def apply_simple(self, p, q):
+        _check(load().schur_apply_simple(self._h, _ptr(p), _ptr(q)))
+
+    def solve_A(self, b, x, tol=1e-12, max_iter=20000):
+        it = C.c_int()
+        _check(load().schur_solve_A(self._h, _ptr(b), _ptr(x), tol, max_iter, C.byref(it)))
+        return it.value
+
+    def time_kernel(self, name) -> float:
+        """Milliseconds of one launch of a hot kernel (CUDA events on the handle stream)."""
+        ms = C.c_float()
+        _check(load().schur_time_kernel(self._h, KERNELS[name], C.byref(ms)))
+        return ms.value
+
+    # ---- layout helpers ----
+    @property
+    def face_stride(self) -> int:
+        return int(self.info.face_stride)
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.info.n_cells)
+
+    def faces_to_grid(self, t):
+        """Face-space tensor [d*stride] -> [d, *shape] view (drops the padding)."""
+        d, s, n = self.ndim, self.face_stride, self.n_cells
+        return t.view(d, s)[:, :n].reshape((d,) + self.shape)

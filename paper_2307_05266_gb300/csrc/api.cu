@@ -1,0 +1,583 @@
+// C ABI of the solver: handle lifetime, device memory, graph instantiation and launch.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/schur.h"
+#include "internal.h"
+
+using namespace schur;
+
+struct schur_geom {
+    Handle H;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char* what) {
+    return set_error(SCHUR_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(expr, what)                                  \
+    do {                                                      \
+        cudaError_t e_ = (expr);                              \
+        if (e_ != cudaSuccess) return cuda_error(e_, what);   \
+    } while (0)
+
+constexpr int kHostSlotBase = 24;  // host-driven loops reuse slots 24..31 on every call
+
+template <class T>
+cudaError_t alloc(Handle& H, T** p, size_t n) {
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T) + 16);
+    if (e == cudaSuccess) {
+        H.bytes += (long long)(n * sizeof(T));
+        e = cudaMemsetAsync(*p, 0, n * sizeof(T), H.stream);
+    }
+    return e;
+}
+
+void free_all(Handle& H) {
+    for (int k = 0; k < 2; ++k) {
+        if (H.exec_solve[k]) cudaGraphExecDestroy(H.exec_solve[k]);
+        if (H.graph_solve[k]) cudaGraphDestroy(H.graph_solve[k]);
+        H.exec_solve[k] = nullptr;
+        H.graph_solve[k] = nullptr;
+    }
+    if (H.exec_recover) cudaGraphExecDestroy(H.exec_recover);
+    if (H.graph_recover) cudaGraphDestroy(H.graph_recover);
+    if (H.exec_solo) cudaGraphExecDestroy(H.exec_solo);
+    if (H.graph_solo) cudaGraphDestroy(H.graph_solo);
+    H.exec_recover = H.exec_solo = nullptr;
+    H.graph_recover = H.graph_solo = nullptr;
+    void* bufs[] = {H.mask, H.flags, H.invdS, H.ax, H.ar, H.ap, H.aq, H.sx, H.sr, H.sp,
+                    H.sq, H.op, H.orr, H.od, H.oq, H.og, H.u, H.partials, H.dctl,
+                    H.cmp, H.cmean, H.small_start, H.small_cells};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (H.hctl) cudaFreeHost(H.hctl);
+    if (H.ev0) cudaEventDestroy(H.ev0);
+    if (H.ev1) cudaEventDestroy(H.ev1);
+}
+
+// Connected fluid components (two fluid cells are connected when the face between them
+// is an unknown; periodic axes wrap), labelled on the host by union-find with the
+// smaller index as root, so labels do not depend on the visiting order.  The largest
+// components (at most kMaxBig, each of at least kBigMin cells) get ids 0..n_big-1 and are
+// reduced by the whole grid; every other component is summed by one warp over its cell
+// list.  Uploads cmp, small_start, small_cells and allocates cmean.
+int build_components(Handle& H, const uint8_t* m) {
+    const Dev& g = H.g;
+    const long long n = g.ncell;
+    std::vector<int> parent((size_t)n);
+    for (long long c = 0; c < n; ++c) parent[c] = (m[c] == 1) ? (int)c : -1;
+    auto find = [&](int x) {
+        while (parent[x] != x) {
+            parent[x] = parent[parent[x]];
+            x = parent[x];
+        }
+        return x;
+    };
+    auto unite = [&](int a, int b) {
+        a = find(a);
+        b = find(b);
+        if (a == b) return;
+        if (a < b) parent[b] = a; else parent[a] = b;
+    };
+    for (int z = 0; z < g.nz; ++z)
+        for (int y = 0; y < g.ny; ++y)
+            for (int x = 0; x < g.nx; ++x) {
+                const long long c = ((long long)z * g.ny + y) * g.nx + x;
+                if (m[c] != 1) continue;
+                for (int a = 0; a < g.d; ++a) {
+                    int lx = x - (a == 0), ly = y - (a == 1), lz = z - (a == 2);
+                    if (lx < 0) { if (!g.per[0]) continue; lx += g.nx; }
+                    if (ly < 0) { if (!g.per[1]) continue; ly += g.ny; }
+                    if (lz < 0) { if (!g.per[2]) continue; lz += g.nz; }
+                    const long long l = ((long long)lz * g.ny + ly) * g.nx + lx;
+                    if (m[l] == 1) unite((int)c, (int)l);
+                }
+            }
+    std::vector<int> first_id((size_t)n, -1);
+    std::vector<long long> size;
+    std::vector<int> comp((size_t)n, -1);
+    for (long long c = 0; c < n; ++c) {
+        if (parent[c] < 0) continue;
+        const int r = find((int)c);
+        if (r == c) {
+            first_id[c] = (int)size.size();
+            size.push_back(0);
+        }
+        comp[c] = first_id[r];
+        size[comp[c]]++;
+    }
+    const int ncomp = (int)size.size();
+    std::vector<int> order(ncomp);
+    std::iota(order.begin(), order.end(), 0);
+    const int ntop = std::min(ncomp, kMaxBig);
+    std::partial_sort(order.begin(), order.begin() + ntop, order.end(), [&](int a, int b) {
+        return size[a] != size[b] ? size[a] > size[b] : a < b;
+    });
+    std::vector<int> remap(ncomp, -1);
+    int nbig = 0;
+    for (int i = 0; i < ntop; ++i)
+        if (size[order[i]] >= kBigMin) {
+            H.hctl->big_size[nbig] = (double)size[order[i]];
+            remap[order[i]] = nbig++;
+        }
+    int next = nbig;
+    for (int k = 0; k < ncomp; ++k)
+        if (remap[k] < 0) remap[k] = next++;
+    const int nsmall = ncomp - nbig;
+    std::vector<int> start((size_t)nsmall + 1, 0);
+    for (long long c = 0; c < n; ++c) {
+        if (comp[c] < 0) continue;
+        comp[c] = remap[comp[c]];
+        if (comp[c] >= nbig) start[comp[c] - nbig + 1]++;
+    }
+    for (int j = 0; j < nsmall; ++j) start[j + 1] += start[j];
+    std::vector<int> cells((size_t)std::max(start[nsmall], 1));
+    std::vector<int> fill(start.begin(), start.end() - 1);
+    for (long long c = 0; c < n; ++c)
+        if (comp[c] >= nbig) cells[fill[comp[c] - nbig]++] = (int)c;
+    H.n_comp = ncomp;
+    H.n_big = nbig;
+    H.n_small = nsmall;
+    cudaError_t e = alloc(H, &H.cmp, (size_t)n);
+    if (e == cudaSuccess) e = alloc(H, &H.cmean, (size_t)std::max(ncomp, 1));
+    if (e == cudaSuccess) e = alloc(H, &H.small_start, start.size());
+    if (e == cudaSuccess) e = alloc(H, &H.small_cells, cells.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(H.cmp, comp.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, H.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(H.small_start, start.data(), start.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, H.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(H.small_cells, cells.data(), cells.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, H.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(H.stream);  // host vectors go out of scope
+    if (e == cudaErrorMemoryAllocation) return set_error(SCHUR_ENOMEM, "device allocation failed");
+    if (e != cudaSuccess) return cuda_error(e, "component upload");
+    return SCHUR_OK;
+}
+
+// Build and instantiate one graph with recorder function `rec`.
+template <class F>
+int build_graph(Handle& H, cudaGraph_t* graph, cudaGraphExec_t* exec, F rec) {
+    if (*exec) return SCHUR_OK;
+    CUDA_TRY(cudaGraphCreate(graph, 0), "cudaGraphCreate");
+    const size_t before = H.handles.size();
+    Recorder R(*graph, H.dctl, &H.next_slot, &H.handles);
+    rec(R);
+    if (!R.ok()) return cuda_error(R.error(), ("graph recording: " + R.where()).c_str());
+    for (size_t k = before; k < H.handles.size(); ++k)
+        H.hctl->handle[H.handles[k].first] = H.handles[k].second;
+    CUDA_TRY(cudaGraphInstantiate(exec, *graph, 0), "cudaGraphInstantiate");
+    return SCHUR_OK;
+}
+
+void reset_call(Handle& H, int use_graph) {
+    Ctl* c = H.hctl;
+    c->use_graph = use_graph;
+    c->f[0] = H.force[0];
+    c->f[1] = H.force[1];
+    c->f[2] = H.force[2];
+    c->launches = 0;
+    c->inner_status = 0;
+    c->ticket = 0;
+    c->inA.total = c->inS.total = c->out.total = c->solo.total = 0;
+}
+
+int upload(Handle& H) {
+    CUDA_TRY(cudaMemcpyAsync(H.dctl, H.hctl, sizeof(Ctl), cudaMemcpyHostToDevice, H.stream),
+             "control upload");
+    return SCHUR_OK;
+}
+
+int download(Handle& H) {
+    CUDA_TRY(cudaMemcpyAsync(H.hctl, H.dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, H.stream),
+             "control download");
+    CUDA_TRY(cudaStreamSynchronize(H.stream), "stream synchronize");
+    return SCHUR_OK;
+}
+
+int map_status(int st) {
+    if (st == ST_OK) return SCHUR_OK;
+    if (st == ST_BREAKDOWN) return SCHUR_EBREAKDOWN;
+    return SCHUR_ENOTCONV;
+}
+
+}  // namespace
+
+extern "C" {
+
+void schur_opts_default(schur_opts* o) {
+    if (!o) return;
+    o->precond = SCHUR_SIMPLE;
+    o->stop_norm = SCHUR_STOP_UNPRECOND;
+    o->precision = SCHUR_FP64;
+    o->loop_mode = SCHUR_LOOP_GRAPH;
+    o->max_outer = 2000;
+    o->max_inner = 20000;
+    o->tol = 1e-8;
+    o->tol_inner_A = 1e-12;
+    o->tol_inner_S = 1e-12;
+}
+
+const char* schur_last_error(void) { return g_last_error.c_str(); }
+
+int schur_create_geometry(const uint8_t* mask, int ndim, const int64_t dims[3],
+                          const int periodic[3], void* stream, schur_geom_t* out) {
+    if (!out) return set_error(SCHUR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!mask || !dims || !periodic) return set_error(SCHUR_EINVAL, "mask, dims or periodic is NULL");
+    if (ndim != 2 && ndim != 3) return set_error(SCHUR_EINVAL, "ndim must be 2 or 3");
+    for (int a = 0; a < ndim; ++a)
+        if (dims[a] < 2 || dims[a] > (1 << 20))
+            return set_error(SCHUR_EINVAL, "every extent must lie in [2, 2^20]");
+    const long long nz = ndim == 3 ? dims[2] : 1;
+    const long long ncell = dims[0] * dims[1] * nz;
+    if (ncell > 2147483647ll) return set_error(SCHUR_EINVAL, "grid too large (cells >= 2^31)");
+
+    schur_geom* G = new schur_geom();
+    Handle& H = G->H;
+    H.stream = (cudaStream_t)stream;
+    Dev& g = H.g;
+    g.nx = (int)dims[0];
+    g.ny = (int)dims[1];
+    g.nz = (int)nz;
+    g.d = ndim;
+    g.per[0] = periodic[0] != 0;
+    g.per[1] = periodic[1] != 0;
+    g.per[2] = ndim == 3 ? periodic[2] != 0 : 1;
+    g.ncell = ncell;
+    g.stride = round_up(ncell, 64);
+    g.h = 1.0 / (double)g.nx;
+    g.hinv = (double)g.nx;
+    g.h2 = g.h * g.h;
+    g.h2inv = g.hinv * g.hinv;
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&H.nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete G;
+        return cuda_error(e, "device query");
+    }
+    H.target_blocks = H.nsm * 8 < kMaxBlocks ? H.nsm * 8 : kMaxBlocks;
+
+    const size_t nf = (size_t)g.d * g.stride;
+    const size_t nc = (size_t)ncell;
+    cudaError_t ea = cudaSuccess;
+    auto A = [&](auto** p, size_t n) { if (ea == cudaSuccess) ea = alloc(H, p, n); };
+    A(&H.mask, nc);
+    A(&H.flags, nf);
+    A(&H.invdS, nc);
+    A(&H.ax, nf); A(&H.ar, nf); A(&H.ap, nf); A(&H.aq, nf);
+    A(&H.sx, nc); A(&H.sr, nc); A(&H.sp, nc); A(&H.sq, nc);
+    A(&H.op, nc); A(&H.orr, nc); A(&H.od, nc); A(&H.oq, nc); A(&H.og, nc);
+    A(&H.u, nf);
+    A(&H.partials, (size_t)kMaxBlocks * 8);
+    A(&H.dctl, 1);
+    if (ea == cudaSuccess) ea = cudaMallocHost((void**)&H.hctl, sizeof(Ctl));
+    if (ea != cudaSuccess) {
+        free_all(H);
+        delete G;
+        if (ea == cudaErrorMemoryAllocation)
+            return set_error(SCHUR_ENOMEM, "device allocation failed");
+        return cuda_error(ea, "allocation");
+    }
+    std::memset(H.hctl, 0, sizeof(Ctl));
+
+    // mask: host or device pointer
+    cudaPointerAttributes attr;
+    cudaMemcpyKind kind = cudaMemcpyHostToDevice;
+    if (cudaPointerGetAttributes(&attr, mask) == cudaSuccess &&
+        (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged))
+        kind = cudaMemcpyDeviceToDevice;
+    cudaGetLastError();
+    e = cudaMemcpyAsync(H.mask, mask, nc, kind, H.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(H.dctl, H.hctl, sizeof(Ctl), cudaMemcpyHostToDevice, H.stream);
+    if (e == cudaSuccess) e = launch_flags(H);
+    if (e == cudaSuccess) e = launch_invdiag_simple(H);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(H.hctl, H.dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, H.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(H.stream);
+    if (e != cudaSuccess) {
+        int rc = cuda_error(e, "geometry build");
+        free_all(H);
+        delete G;
+        return rc;
+    }
+    if (H.hctl->counts[4] != 0.0) {
+        free_all(H);
+        delete G;
+        return set_error(SCHUR_EINVAL, "mask values must be 0 (solid) or 1 (fluid)");
+    }
+    // components are labelled on the host
+    std::vector<uint8_t> hmask;
+    const uint8_t* hm = mask;
+    if (kind == cudaMemcpyDeviceToDevice) {
+        hmask.resize(nc);
+        e = cudaMemcpy(hmask.data(), H.mask, nc, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            int rc = cuda_error(e, "mask download");
+            free_all(H);
+            delete G;
+            return rc;
+        }
+        hm = hmask.data();
+    }
+    int rc = build_components(H, hm);
+    if (rc == SCHUR_OK) rc = upload(H);
+    if (rc == SCHUR_OK) {
+        e = cudaStreamSynchronize(H.stream);
+        if (e != cudaSuccess) rc = cuda_error(e, "geometry build");
+    }
+    if (rc != SCHUR_OK) {
+        free_all(H);
+        delete G;
+        return rc;
+    }
+    *out = G;
+    return SCHUR_OK;
+}
+
+int schur_set_force(schur_geom_t G, const double f[3]) {
+    if (!G || !f) return set_error(SCHUR_EINVAL, "null argument");
+    for (int a = 0; a < 3; ++a) {
+        if (!std::isfinite(f[a])) return set_error(SCHUR_EINVAL, "force must be finite");
+        G->H.force[a] = (a < G->H.g.d) ? f[a] : 0.0;
+    }
+    G->H.solved = G->H.recovered = false;
+    return SCHUR_OK;
+}
+
+int schur_solve(schur_geom_t G, const schur_opts* opts, schur_stats* stats) {
+    if (!G) return set_error(SCHUR_EINVAL, "null handle");
+    schur_opts o;
+    if (opts) o = *opts; else schur_opts_default(&o);
+    if (o.precond != SCHUR_UZAWA && o.precond != SCHUR_SIMPLE)
+        return set_error(SCHUR_EINVAL, "precond must be SCHUR_UZAWA or SCHUR_SIMPLE");
+    if (o.stop_norm != SCHUR_STOP_UNPRECOND && o.stop_norm != SCHUR_STOP_PRECOND)
+        return set_error(SCHUR_EINVAL, "bad stop_norm");
+    if (o.precision != SCHUR_FP64) return set_error(SCHUR_EINVAL, "only SCHUR_FP64 is available");
+    if (o.loop_mode != SCHUR_LOOP_GRAPH && o.loop_mode != SCHUR_LOOP_HOST)
+        return set_error(SCHUR_EINVAL, "bad loop_mode");
+    if (!(o.tol > 0) || !(o.tol_inner_A > 0) || !(o.tol_inner_S > 0) || o.max_outer < 1 ||
+        o.max_inner < 1)
+        return set_error(SCHUR_EINVAL, "tolerances must be > 0 and caps >= 1");
+    Handle& H = G->H;
+    Ctl* c = H.hctl;
+    reset_call(H, o.loop_mode == SCHUR_LOOP_GRAPH);
+    c->precond = o.precond;
+    c->stop_norm = o.stop_norm;
+    c->inA.tol = o.tol_inner_A;
+    c->inA.max_iter = o.max_inner;
+    c->inS.tol = o.tol_inner_S;
+    c->inS.max_iter = o.max_inner;
+    c->out.tol = o.tol;
+    c->out.max_iter = o.max_outer;
+    c->zero_rhs = 0;
+    int rc;
+    if (o.loop_mode == SCHUR_LOOP_GRAPH) {
+        rc = build_graph(H, &H.graph_solve[o.precond], &H.exec_solve[o.precond],
+                         [&](Recorder& R) { record_solve(H, R, o.precond); });
+        if (rc) return rc;
+        if ((rc = upload(H))) return rc;
+        CUDA_TRY(cudaGraphLaunch(H.exec_solve[o.precond], H.stream), "cudaGraphLaunch");
+    } else {
+        if ((rc = upload(H))) return rc;
+        int slot = kHostSlotBase;
+        Recorder R(H.stream, H.dctl, &slot);
+        record_solve(H, R, o.precond);
+        if (!R.ok()) return cuda_error(R.error(), R.where().c_str());
+    }
+    if ((rc = download(H))) return rc;
+    H.solved = true;
+    H.recovered = false;
+    H.last_tolA = o.tol_inner_A;
+    H.last_max_inner = o.max_inner;
+    H.last_loop = o.loop_mode;
+    if (stats) {
+        stats->status = map_status(c->out.status);
+        stats->outer_iters = c->out.iter;
+        stats->zero_rhs = c->zero_rhs;
+        stats->inner_status = map_status(c->inner_status);
+        stats->inner_iters_A = c->inA.total;
+        stats->inner_iters_S = c->inS.total;
+        stats->rel_res = c->out.rel;
+        stats->rel_res_precond = c->out.relz;
+        stats->g_norm = std::sqrt(c->g_norm2);
+        stats->kernel_launches = c->launches;
+    }
+    const int st = map_status(c->out.status);
+    if (st != SCHUR_OK) set_error(st, "outer iteration did not converge");
+    return st;
+}
+
+int schur_recover_velocity(schur_geom_t G, schur_stats* stats) {
+    if (!G) return set_error(SCHUR_EINVAL, "null handle");
+    Handle& H = G->H;
+    if (!H.solved) return set_error(SCHUR_ESTATE, "recover_velocity needs a schur_solve first");
+    Ctl* c = H.hctl;
+    reset_call(H, H.last_loop == SCHUR_LOOP_GRAPH);
+    c->inA.tol = H.last_tolA;
+    c->inA.max_iter = H.last_max_inner;
+    int rc;
+    if (H.last_loop == SCHUR_LOOP_GRAPH) {
+        rc = build_graph(H, &H.graph_recover, &H.exec_recover,
+                         [&](Recorder& R) { record_recover(H, R); });
+        if (rc) return rc;
+        if ((rc = upload(H))) return rc;
+        CUDA_TRY(cudaGraphLaunch(H.exec_recover, H.stream), "cudaGraphLaunch");
+    } else {
+        if ((rc = upload(H))) return rc;
+        int slot = kHostSlotBase;
+        Recorder R(H.stream, H.dctl, &slot);
+        record_recover(H, R);
+        if (!R.ok()) return cuda_error(R.error(), R.where().c_str());
+    }
+    if ((rc = download(H))) return rc;
+    H.recovered = true;
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->status = map_status(c->inA.status);
+        stats->inner_status = map_status(c->inner_status);
+        stats->inner_iters_A = c->inA.total;
+        stats->rel_res = c->inA.rel;
+        stats->kernel_launches = c->launches;
+    }
+    const int st = map_status(c->inA.status);
+    if (st != SCHUR_OK) set_error(st, "velocity recovery did not converge");
+    return st;
+}
+
+int schur_permeability(schur_geom_t G, int axis, double* k_out) {
+    if (!G || !k_out) return set_error(SCHUR_EINVAL, "null argument");
+    Handle& H = G->H;
+    if (axis < 0 || axis >= H.g.d) return set_error(SCHUR_EINVAL, "axis out of range");
+    if (!H.recovered) return set_error(SCHUR_ESTATE, "permeability needs recover_velocity first");
+    *k_out = H.hctl->perm[axis];
+    return SCHUR_OK;
+}
+
+int schur_get_field(schur_geom_t G, int which, void** dev_ptr, int64_t* elems, int* dtype) {
+    if (!G || !dev_ptr) return set_error(SCHUR_EINVAL, "null argument");
+    Handle& H = G->H;
+    const int64_t nf = (int64_t)H.g.d * H.g.stride, nc = H.g.ncell;
+    void* p = nullptr;
+    int64_t n = 0;
+    int dt = 0;
+    switch (which) {
+        case SCHUR_FIELD_P: p = H.op; n = nc; dt = SCHUR_DTYPE_F64; break;
+        case SCHUR_FIELD_U: p = H.u; n = nf; dt = SCHUR_DTYPE_F64; break;
+        case SCHUR_FIELD_FLAGS: p = H.flags; n = nf; dt = SCHUR_DTYPE_U8; break;
+        case SCHUR_FIELD_MASK: p = H.mask; n = nc; dt = SCHUR_DTYPE_U8; break;
+        case SCHUR_FIELD_G: p = H.og; n = nc; dt = SCHUR_DTYPE_F64; break;
+        default: return set_error(SCHUR_EINVAL, "unknown field");
+    }
+    *dev_ptr = p;
+    if (elems) *elems = n;
+    if (dtype) *dtype = dt;
+    return SCHUR_OK;
+}
+
+int schur_geometry_info(schur_geom_t G, schur_geom_info* info) {
+    if (!G || !info) return set_error(SCHUR_EINVAL, "null argument");
+    Handle& H = G->H;
+    std::memset(info, 0, sizeof(*info));
+    info->ndim = H.g.d;
+    info->dims[0] = H.g.nx;
+    info->dims[1] = H.g.ny;
+    info->dims[2] = H.g.d == 3 ? H.g.nz : 1;
+    for (int a = 0; a < 3; ++a) info->periodic[a] = H.g.per[a];
+    info->n_cells = H.g.ncell;
+    info->face_stride = H.g.stride;
+    for (int a = 0; a < 3; ++a) info->n_unknown[a] = (int64_t)H.hctl->counts[a];
+    info->n_fluid = (int64_t)H.hctl->counts[3];
+    info->h = H.g.h;
+    info->device_bytes = H.bytes;
+    return SCHUR_OK;
+}
+
+int schur_apply_A(schur_geom_t G, const double* x, double* y) {
+    if (!G || !x || !y) return set_error(SCHUR_EINVAL, "null argument");
+    cudaError_t e = launch_apply_A(G->H, x, y);
+    return e == cudaSuccess ? SCHUR_OK : cuda_error(e, "apply_A");
+}
+
+int schur_apply_B(schur_geom_t G, const double* u, double* p) {
+    if (!G || !u || !p) return set_error(SCHUR_EINVAL, "null argument");
+    cudaError_t e = launch_apply_B(G->H, u, p);
+    return e == cudaSuccess ? SCHUR_OK : cuda_error(e, "apply_B");
+}
+
+int schur_apply_BT(schur_geom_t G, const double* p, double* u) {
+    if (!G || !p || !u) return set_error(SCHUR_EINVAL, "null argument");
+    cudaError_t e = launch_apply_BT(G->H, p, u);
+    return e == cudaSuccess ? SCHUR_OK : cuda_error(e, "apply_BT");
+}
+
+int schur_apply_simple(schur_geom_t G, const double* p, double* q) {
+    if (!G || !p || !q) return set_error(SCHUR_EINVAL, "null argument");
+    cudaError_t e = launch_apply_simple(G->H, p, q);
+    return e == cudaSuccess ? SCHUR_OK : cuda_error(e, "apply_simple");
+}
+
+int schur_solve_A(schur_geom_t G, const double* b, double* x, double tol, int max_iter,
+                  int* iters) {
+    if (!G || !b || !x) return set_error(SCHUR_EINVAL, "null argument");
+    if (!(tol > 0) || max_iter < 1) return set_error(SCHUR_EINVAL, "tol must be > 0, max_iter >= 1");
+    Handle& H = G->H;
+    const size_t nf = (size_t)H.g.d * H.g.stride;
+    Ctl* c = H.hctl;
+    reset_call(H, 1);
+    c->solo.tol = tol;
+    c->solo.max_iter = max_iter;
+    // the right-hand side is staged in aq (matvec output, rewritten before use)
+    CUDA_TRY(cudaMemcpyAsync(H.aq, b, nf * sizeof(double), cudaMemcpyDeviceToDevice, H.stream),
+             "stage rhs");
+    int rc = build_graph(H, &H.graph_solo, &H.exec_solo,
+                         [&](Recorder& R) { record_solve_A(H, R, H.aq, H.ax); });
+    if (rc) return rc;
+    if ((rc = upload(H))) return rc;
+    CUDA_TRY(cudaGraphLaunch(H.exec_solo, H.stream), "cudaGraphLaunch");
+    CUDA_TRY(cudaMemcpyAsync(x, H.ax, nf * sizeof(double), cudaMemcpyDeviceToDevice, H.stream),
+             "copy solution");
+    if ((rc = download(H))) return rc;
+    if (iters) *iters = c->solo.iter;
+    const int st = map_status(c->solo.status);
+    if (st != SCHUR_OK) set_error(st, "inner A solve did not converge");
+    return st;
+}
+
+int schur_time_kernel(schur_geom_t G, int kernel, float* ms) {
+    if (!G || !ms) return set_error(SCHUR_EINVAL, "null argument");
+    if (kernel < 0 || kernel > 5) return set_error(SCHUR_EINVAL, "kernel id must be 0..5");
+    Handle& H = G->H;
+    reset_call(H, 0);  // no graph: the condition slot is only written to device memory
+    int rc = upload(H);
+    if (rc) return rc;
+    cudaError_t e = time_kernel(H, kernel, kSlots - 1, ms);
+    if (e != cudaSuccess) return cuda_error(e, "time_kernel");
+    return download(H);
+}
+
+void schur_destroy(schur_geom_t G) {
+    if (!G) return;
+    cudaStreamSynchronize(G->H.stream);
+    free_all(G->H);
+    delete G;
+}
+
+}  // extern "C"

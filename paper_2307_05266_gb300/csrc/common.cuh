@@ -1,0 +1,287 @@
+// Shared device/host definitions of the GB300 Schur-complement Stokes solver.
+//
+// Layout in HBM (all buffers owned by one geometry handle):
+//   mask   uint8  [n_cells]            C order [z][y][x], 1 = fluid
+//   flags  uint8  [d][stride]          face (a, c) = lower face of cell c along axis a;
+//                                      bit 0 unknown, bits 1..3 ghost (solid-solid) count
+//   face vectors  T [d][stride]        0 on faces that are not unknowns
+//   cell vectors  T [n_cells]          0 on solid cells
+// stride = n_cells rounded up to 64 elements, so every component starts 512-byte aligned.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <functional>
+#include <string>
+#include <vector>
+
+namespace schur {
+
+constexpr int kTileX = 32;             // threads along x in stencil tiles (one warp row)
+constexpr int kTileY = 8;              // rows of a stencil tile
+constexpr int kBlock = kTileX * kTileY;
+constexpr int kMaxRed = 4;             // doubles reduced by one kernel at most
+constexpr int kMaxBlocks = 4096;       // grid cap of every reducing kernel
+constexpr int kSlots = 32;             // loop-condition slots per handle
+constexpr double kZeroRhsRtol = 1e-12; // g == 0 when ||g|| <= this * || |B| |u| ||
+constexpr int kMaxBig = 8;             // fluid components reduced by the full grid
+constexpr long long kBigMin = 2048;    // smallest component treated as "big"
+
+enum Status : int { ST_OK = 0, ST_NOTCONV = 3, ST_BREAKDOWN = 4 };
+
+struct Dev {
+    int nx, ny, nz, d;
+    int per[3];
+    long long ncell;
+    long long stride;
+    double h, hinv, h2inv, h2;
+};
+
+// One Krylov instance (inner A solve, inner SIMPLE solve, outer Schur CG).
+struct CgState {
+    double tol;
+    int max_iter;
+    int iter;
+    int status;
+    int first;        // 1 until the first direction update has used beta = 0
+    int done;         // outer: converged / stopped; inner: unused
+    int skip_next;    // outer: the S-hat solve of this iteration is skipped
+    int cap;          // outer: the iteration cap was reached in this iteration
+    double rho;       // r . z
+    double alpha, beta;
+    double zz0;       // ||z_0||^2 (inner: preconditioned residual)
+    double rr0;       // outer: ||r_0||^2
+    double rel;       // inner: ||z||/||z_0||; outer: ||r||/||r_0||
+    double relz;      // outer: ||z||/||z_0||
+    long long total;  // iterations summed over every solve of this kind in the call
+};
+
+struct Ctl {
+    // options (host-written before a launch)
+    int precond, stop_norm, use_graph, pad0;
+    double f[3];
+    // loop conditions
+    unsigned long long handle[kSlots];
+    unsigned int cond[kSlots];
+    // Krylov instances
+    CgState inA, inS, out, solo;
+    // results
+    double g_norm2, g_scale2;
+    int zero_rhs, inner_status;
+    double perm[3];
+    double counts[5];  // unknown faces x/y/z, fluid cells, invalid mask bytes
+    double n_fluid;    // fluid cells
+    double big_size[kMaxBig];  // cells of each big fluid component
+    long long launches;
+    unsigned int ticket;
+    unsigned int pad1;
+};
+
+inline long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+// ---- device helpers ---------------------------------------------------------------
+
+// Cell index of (x + dx, y + dy, z + dz) with periodic wrap; -1 outside a closed box.
+// Offsets are at most one cell, so one wrap suffices.
+__device__ __forceinline__ long long cell_at(const Dev& g, int x, int y, int z) {
+    if (x < 0) { if (!g.per[0]) return -1; x += g.nx; } else if (x >= g.nx) { if (!g.per[0]) return -1; x -= g.nx; }
+    if (y < 0) { if (!g.per[1]) return -1; y += g.ny; } else if (y >= g.ny) { if (!g.per[1]) return -1; y -= g.ny; }
+    if (z < 0) { if (!g.per[2]) return -1; z += g.nz; } else if (z >= g.nz) { if (!g.per[2]) return -1; z -= g.nz; }
+    return ((long long)z * g.ny + y) * g.nx + x;
+}
+
+__device__ __forceinline__ void axis_step(int a, int s, int& dx, int& dy, int& dz) {
+    dx = (a == 0) ? s : 0;
+    dy = (a == 1) ? s : 0;
+    dz = (a == 2) ? s : 0;
+}
+
+__device__ __forceinline__ void count_launch(Ctl* ctl) {
+    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0 && blockIdx.x == 0 &&
+        blockIdx.y == 0 && blockIdx.z == 0)
+        atomicAdd((unsigned long long*)&ctl->launches, 1ull);
+}
+
+__device__ __forceinline__ void set_cond(Ctl* ctl, int slot, unsigned v) {
+    ctl->cond[slot] = v;
+    if (ctl->use_graph) cudaGraphSetConditional(ctl->handle[slot], v);
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Block-sum K doubles; every block writes its partial sums, and the block that finishes
+// last sums all partials in a fixed order (deterministic for a fixed grid), resets the
+// ticket and returns true with the totals in v[] for all its threads.
+template <int K>
+__device__ __forceinline__ bool reduce_last_block(double (&v)[K], double* partials,
+                                                  unsigned int* ticket) {
+    __shared__ double sm[K][32];
+    __shared__ unsigned int s_last;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double x = warp_sum(v[k]);
+        if (lane == 0) sm[k][warp] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double x = warp_sum(lane < nwarp ? sm[k][lane] : 0.0);
+            if (lane == 0) partials[(size_t)bid * K + k] = x;
+        }
+        if (lane == 0) {
+            __threadfence();
+            unsigned prev = atomicAdd(ticket, 1u);
+            s_last = (prev == nblk - 1) ? 1u : 0u;
+        }
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    for (unsigned i = tid; i < nblk; i += nthr) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] += __ldcg(&partials[(size_t)i * K + k]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double x = warp_sum(acc[k]);
+        if (lane == 0) sm[k][warp] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double x = warp_sum(lane < nwarp ? sm[k][lane] : 0.0);
+            if (lane == 0) sm[k][0] = x;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = sm[k][0];
+    if (tid == 0) *ticket = 0u;
+    return true;
+}
+
+// ---- launch recorder: direct launches on a stream, or nodes of a CUDA graph -------
+
+template <class T> struct ident { using type = T; };
+
+class Recorder {
+  public:
+    // host-driven mode: kernels launch on `stream`, loops poll ctl->cond on the host
+    Recorder(cudaStream_t stream, Ctl* dctl, int* next_slot)
+        : stream_(stream), graph_(nullptr), dctl_(dctl), next_slot_(next_slot) {}
+    // graph mode: kernels become nodes of `graph`, loops become conditional while nodes
+    Recorder(cudaGraph_t graph, Ctl* dctl, int* next_slot,
+             std::vector<std::pair<int, unsigned long long>>* handles)
+        : stream_(nullptr), graph_(graph), dctl_(dctl), next_slot_(next_slot),
+          handles_(handles) {}
+
+    bool ok() const { return err_ == cudaSuccess; }
+    cudaError_t error() const { return err_; }
+    const std::string& where() const { return where_; }
+
+    int new_slot() {
+        int s = (*next_slot_)++;
+        if (s >= kSlots) fail(cudaErrorInvalidValue, "out of loop slots");
+        return s < kSlots ? s : kSlots - 1;
+    }
+
+    template <typename... P>
+    void launch(const char* name, void (*k)(P...), dim3 grid, dim3 block,
+                typename ident<P>::type... args) {
+        if (!ok()) return;
+        if (!graph_) {
+            k<<<grid, block, 0, stream_>>>(args...);
+            check(cudaGetLastError(), name);
+            return;
+        }
+        void* ptrs[sizeof...(P) + 1] = {(void*)&args...};
+        cudaKernelNodeParams p = {};
+        p.func = (void*)k;
+        p.gridDim = grid;
+        p.blockDim = block;
+        p.sharedMemBytes = 0;
+        p.kernelParams = ptrs;
+        cudaGraphNode_t node;
+        check(cudaGraphAddKernelNode(&node, graph_, have_last_ ? &last_ : nullptr,
+                                     have_last_ ? 1 : 0, &p), name);
+        last_ = node;
+        have_last_ = true;
+    }
+
+    // while (ctl->cond[slot]) body();  -- the kernel recorded just before the loop and
+    // the last kernel of the body set the condition.
+    void loop(int slot, const std::function<void(Recorder&)>& body) {
+        if (!ok()) return;
+        if (!graph_) {
+            for (;;) {
+                unsigned c = 0;
+                check(cudaMemcpyAsync(&c, &dctl_->cond[slot], sizeof(c), cudaMemcpyDeviceToHost,
+                                      stream_), "loop condition read");
+                check(cudaStreamSynchronize(stream_), "loop condition sync");
+                if (!ok() || !c) break;
+                body(*this);
+                if (!ok()) break;
+            }
+            return;
+        }
+        cudaGraphConditionalHandle h;
+        check(cudaGraphConditionalHandleCreate(&h, graph_, 0, 0), "conditional handle");
+        if (!ok()) return;
+        handles_->push_back({slot, (unsigned long long)h});
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        check(cudaGraphAddNode(&node, graph_, have_last_ ? &last_ : nullptr, nullptr,
+                               have_last_ ? 1 : 0, &np), "conditional node");
+        if (!ok()) return;
+        Recorder sub(np.conditional.phGraph_out[0], dctl_, next_slot_, handles_);
+        body(sub);
+        if (!sub.ok()) {
+            err_ = sub.err_;
+            where_ = sub.where_;
+            return;
+        }
+        last_ = node;
+        have_last_ = true;
+    }
+
+  private:
+    void check(cudaError_t e, const char* what) {
+        if (e != cudaSuccess && err_ == cudaSuccess) {
+            err_ = e;
+            where_ = what;
+        }
+    }
+    void fail(cudaError_t e, const char* what) { check(e, what); }
+
+    cudaStream_t stream_;
+    cudaGraph_t graph_;
+    Ctl* dctl_;
+    int* next_slot_;
+    std::vector<std::pair<int, unsigned long long>>* handles_ = nullptr;
+    cudaGraphNode_t last_{};
+    bool have_last_ = false;
+    cudaError_t err_ = cudaSuccess;
+    std::string where_;
+};
+
+}  // namespace schur

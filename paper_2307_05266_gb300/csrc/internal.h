@@ -1,0 +1,74 @@
+// Host-side interface between the C ABI (api.cu) and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+
+namespace schur {
+
+// Device buffers and graphs of one geometry (the object behind schur_geom_t).
+struct Handle {
+    Dev g{};
+    cudaStream_t stream = nullptr;
+    int nsm = 152;
+    int target_blocks = 1216;
+
+    uint8_t* mask = nullptr;     // [ncell]
+    uint8_t* flags = nullptr;    // [d][stride]
+    double* invdS = nullptr;     // [ncell] inverse diagonal of S-hat_simple (0 off fluid)
+    // inner A solve (face space)
+    double *ax = nullptr, *ar = nullptr, *ap = nullptr, *aq = nullptr;
+    // inner SIMPLE solve (cell space)
+    double *sx = nullptr, *sr = nullptr, *sp = nullptr, *sq = nullptr;
+    // outer Schur CG (cell space)
+    double *op = nullptr, *orr = nullptr, *od = nullptr, *oq = nullptr, *og = nullptr;
+    double* u = nullptr;         // recovered velocity [d][stride]
+    // connected fluid components (connectivity through unknown faces)
+    int* cmp = nullptr;          // [ncell] component id, -1 on solid cells
+    double* cmean = nullptr;     // [n_comp] per-component mean of the last projected vector
+    int* small_start = nullptr;  // [n_small + 1] CSR offsets of the small components
+    int* small_cells = nullptr;  // cells of the small components, increasing per component
+    int n_comp = 0, n_big = 0, n_small = 0;
+    double* partials = nullptr;  // reduction scratch
+    Ctl* dctl = nullptr;         // device control block
+    Ctl* hctl = nullptr;         // pinned host shadow
+
+    cudaGraph_t graph_solve[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec_solve[2] = {nullptr, nullptr};
+    cudaGraph_t graph_recover = nullptr;
+    cudaGraphExec_t exec_recover = nullptr;
+    cudaGraph_t graph_solo = nullptr;
+    cudaGraphExec_t exec_solo = nullptr;
+    int next_slot = 0;
+    std::vector<std::pair<int, unsigned long long>> handles;
+
+    double force[3] = {1.0, 0.0, 0.0};
+    bool solved = false, recovered = false;
+    int last_precond = 1, last_stop = 0;
+    double last_tolA = 1e-12;
+    int last_max_inner = 20000;
+    int last_loop = 0;
+    long long bytes = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+// geometry.cu
+cudaError_t launch_flags(Handle& H);
+cudaError_t launch_invdiag_simple(Handle& H);
+cudaError_t launch_apply_A(Handle& H, const double* x, double* y);
+cudaError_t launch_apply_B(Handle& H, const double* u, double* p);
+cudaError_t launch_apply_BT(Handle& H, const double* p, double* u);
+cudaError_t launch_apply_simple(Handle& H, const double* p, double* q);
+
+// krylov.cu: record the control flow of a call into R (graph nodes or direct launches)
+void record_solve(Handle& H, Recorder& R, int precond);
+void record_recover(Handle& H, Recorder& R);
+void record_solve_A(Handle& H, Recorder& R, const double* b, double* x);
+cudaError_t time_kernel(Handle& H, int which, int slot, float* ms);
+
+}  // namespace schur

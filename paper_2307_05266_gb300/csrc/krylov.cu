@@ -1,0 +1,761 @@
+// Krylov kernels and the recorded control flow of a solve.
+//
+// Inner solves: Jacobi-preconditioned CG from x_0 = 0 with the stopping rule of
+// Section 3.2, ||M^-1 r_k|| / ||M^-1 r_0|| < eps, for A (face space, M = diag(A)) and
+// for S-hat_simple (cell space, M = diag(S-hat)).  One CG iteration is three kernels:
+//   dir:    p = z + beta p  (z = M^-1 r formed on the fly; beta = 0 on the first pass)
+//   matvec: q = Op p and the partial sums of p.q; the last block forms alpha = rho/p.q
+//   update: x += alpha p, r -= alpha q, partial sums of r.z and z.z; the last block
+//           forms beta, tests convergence and sets the loop condition.
+// Outer solve: Algorithm 1 with r = g - S p (the printed sign of r^0 and of the r update
+// is inconsistent; standard PCG of Saad Alg. 9.1 is used), p_0 = 0, and either the
+// unpreconditioned ||r_k||/||r_0|| or the preconditioned ||z_k||/||z_0|| stop.
+// All scalars live in the device control block; every loop is a conditional while node
+// of one CUDA graph (or a host loop in debugging mode).  Every loop terminates: each
+// condition update either continues below its iteration cap or stops.
+#include <cmath>
+
+#include "internal.h"
+
+namespace schur {
+
+#define TILE_LOOP_BEGIN(g)                                                        \
+    const int gx_ = ((g).nx + kTileX - 1) / kTileX;                               \
+    const int gy_ = ((g).ny + kTileY - 1) / kTileY;                               \
+    const long long nt_ = (long long)gx_ * gy_ * (g).nz;                          \
+    for (long long t_ = blockIdx.x; t_ < nt_; t_ += gridDim.x) {                  \
+        const int x = (int)(t_ % gx_) * kTileX + (int)threadIdx.x;                \
+        const int y = (int)((t_ / gx_) % gy_) * kTileY + (int)threadIdx.y;        \
+        const int z = (int)(t_ / ((long long)gx_ * gy_));                         \
+        if (x < (g).nx && y < (g).ny) {                                           \
+            const long long c = ((long long)z * (g).ny + y) * (g).nx + x;
+#define TILE_LOOP_END \
+        }             \
+    }
+
+#define STREAM_LOOP(i, n) \
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (n); \
+         i += (long long)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ bool is_thread0() { return threadIdx.x == 0 && threadIdx.y == 0; }
+
+__device__ __forceinline__ double jac_A(const Dev& g, uint8_t f) {
+    // inverse of diag(A)_f = h^-2 (2d + g_f)
+    return g.h2 / (double)(2 * g.d + (f >> 1));
+}
+
+__device__ __forceinline__ double face_val(const Dev& g, const uint8_t* __restrict__ flags,
+                                           const double* __restrict__ u, int a, int x, int y,
+                                           int z) {
+    long long c = cell_at(g, x, y, z);
+    if (c < 0) return 0.0;
+    const long long i = (long long)a * g.stride + c;
+    return (flags[i] & 1) ? u[i] : 0.0;
+}
+
+__device__ __forceinline__ void note_inner_status(Ctl* ctl, int st) {
+    if (st > ctl->inner_status) ctl->inner_status = st;
+}
+
+// Finish an inner CG iteration (last block): returns the new loop condition.
+__device__ __forceinline__ unsigned finish_inner(Ctl* ctl, CgState* st, double rz, double zz) {
+    st->iter += 1;
+    st->total += 1;
+    st->first = 0;
+    if (st->status == ST_BREAKDOWN) { note_inner_status(ctl, ST_BREAKDOWN); return 0u; }
+    const double rel = sqrt(zz / st->zz0);
+    st->rel = rel;
+    if (rel < st->tol) { st->status = ST_OK; return 0u; }
+    if (!(rel == rel)) { st->status = ST_BREAKDOWN; note_inner_status(ctl, ST_BREAKDOWN); return 0u; }
+    if (st->iter >= st->max_iter) { st->status = ST_NOTCONV; note_inner_status(ctl, ST_NOTCONV); return 0u; }
+    st->beta = rz / st->rho;
+    st->rho = rz;
+    return 1u;
+}
+
+__device__ __forceinline__ unsigned start_inner(Ctl* ctl, CgState* st, double rz, double zz) {
+    st->iter = 0;
+    st->first = 1;
+    st->alpha = 0.0;
+    st->beta = 0.0;
+    st->rho = rz;
+    st->zz0 = zz;
+    if (zz == 0.0) { st->status = ST_OK; st->rel = 0.0; return 0u; }
+    if (!(zz == zz) || isinf(zz)) {
+        st->status = ST_BREAKDOWN;
+        note_inner_status(ctl, ST_BREAKDOWN);
+        return 0u;
+    }
+    st->status = ST_NOTCONV;
+    st->rel = 1.0;
+    return 1u;
+}
+
+// ------------------------------------------------------------------------------------
+// inner CG on A (face space)
+// ------------------------------------------------------------------------------------
+
+// b = cf f_a + cp h^-1 (P_c - P_(c-e_a)) (+ bvec) on unknown faces; x = 0, r = b.
+__global__ void k_cgA_init(Dev g, const uint8_t* __restrict__ flags, double* __restrict__ xv,
+                           double* __restrict__ rv, const double* __restrict__ P, double cp,
+                           double cf, const double* __restrict__ bvec, Ctl* ctl, CgState* st,
+                           double* partials, int slot) {
+    count_launch(ctl);
+    double v[2] = {0.0, 0.0};
+    TILE_LOOP_BEGIN(g)
+        for (int a = 0; a < g.d; ++a) {
+            const long long i = (long long)a * g.stride + c;
+            const uint8_t f = flags[i];
+            double b = 0.0;
+            if (f & 1) {
+                b = cf * ctl->f[a];
+                if (P) {
+                    int ex, ey, ez;
+                    axis_step(a, 1, ex, ey, ez);
+                    b += cp * (g.hinv * (P[c] - P[cell_at(g, x - ex, y - ey, z - ez)]));
+                }
+                if (bvec) b += bvec[i];
+                const double zz = b * jac_A(g, f);
+                v[0] += b * zz;
+                v[1] += zz * zz;
+            }
+            xv[i] = 0.0;
+            rv[i] = b;
+        }
+    TILE_LOOP_END
+    if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0())
+        set_cond(ctl, slot, start_inner(ctl, st, v[0], v[1]));
+}
+
+__global__ void k_cgA_dir(Dev g, const uint8_t* __restrict__ flags, const double* __restrict__ rv,
+                          double* __restrict__ pv, Ctl* ctl, const CgState* st) {
+    count_launch(ctl);
+    const double beta = st->first ? 0.0 : st->beta;
+    const long long n = (long long)g.d * g.stride;
+    STREAM_LOOP(i, n) {
+        const uint8_t f = flags[i];
+        double out = 0.0;
+        if (f & 1) out = rv[i] * jac_A(g, f) + beta * pv[i];
+        pv[i] = out;
+    }
+}
+
+__global__ void k_cgA_matvec(Dev g, const uint8_t* __restrict__ flags, const double* __restrict__ pv,
+                             double* __restrict__ qv, Ctl* ctl, CgState* st, double* partials,
+                             int slot) {
+    count_launch(ctl);
+    double v[1] = {0.0};
+    TILE_LOOP_BEGIN(g)
+        for (int a = 0; a < g.d; ++a) {
+            const long long i = (long long)a * g.stride + c;
+            const uint8_t f = flags[i];
+            double out = 0.0;
+            if (f & 1) {
+                double s = face_val(g, flags, pv, a, x - 1, y, z) + face_val(g, flags, pv, a, x + 1, y, z);
+                s += face_val(g, flags, pv, a, x, y - 1, z) + face_val(g, flags, pv, a, x, y + 1, z);
+                if (g.d == 3)
+                    s += face_val(g, flags, pv, a, x, y, z - 1) + face_val(g, flags, pv, a, x, y, z + 1);
+                const double pc = pv[i];
+                out = g.h2inv * ((double)(2 * g.d + (f >> 1)) * pc - s);
+                v[0] += pc * out;
+            }
+            qv[i] = out;
+        }
+    TILE_LOOP_END
+    if (reduce_last_block<1>(v, partials, &ctl->ticket) && is_thread0()) {
+        const double dq = v[0];
+        if (!(dq > 0.0) || isinf(dq)) {
+            st->status = ST_BREAKDOWN;
+            st->alpha = 0.0;
+            set_cond(ctl, slot, 0u);
+        } else {
+            st->alpha = st->rho / dq;
+        }
+    }
+}
+
+__global__ void k_cgA_update(Dev g, const uint8_t* __restrict__ flags, double* __restrict__ xv,
+                             double* __restrict__ rv, const double* __restrict__ pv,
+                             const double* __restrict__ qv, Ctl* ctl, CgState* st,
+                             double* partials, int slot) {
+    count_launch(ctl);
+    const double alpha = st->alpha;
+    double v[2] = {0.0, 0.0};
+    const long long n = (long long)g.d * g.stride;
+    STREAM_LOOP(i, n) {
+        const uint8_t f = flags[i];
+        if (f & 1) {
+            xv[i] += alpha * pv[i];
+            const double r = rv[i] - alpha * qv[i];
+            rv[i] = r;
+            const double zz = r * jac_A(g, f);
+            v[0] += r * zz;
+            v[1] += zz * zz;
+        }
+    }
+    if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0())
+        set_cond(ctl, slot, finish_inner(ctl, st, v[0], v[1]));
+}
+
+// ------------------------------------------------------------------------------------
+// inner CG on S-hat_simple (cell space); M^-1 = invd (0 on solid and isolated cells)
+// ------------------------------------------------------------------------------------
+
+// b = r - (its mean on r's fluid component): r is projected onto the range of S-hat in
+// place, then x = 0 and the CG residual starts at b.
+__global__ void k_cgS_init(Dev g, const double* __restrict__ invd, const int* __restrict__ cmp,
+                           const double* __restrict__ cmean, double* __restrict__ b,
+                           double* __restrict__ xv, double* __restrict__ rv, Ctl* ctl,
+                           CgState* st, const CgState* outer, double* partials, int slot) {
+    count_launch(ctl);
+    if (outer->skip_next) {
+        if (blockIdx.x == 0 && is_thread0()) set_cond(ctl, slot, 0u);
+        return;
+    }
+    double v[2] = {0.0, 0.0};
+    STREAM_LOOP(c, g.ncell) {
+        const int k = cmp[c];
+        double bc = 0.0;
+        if (k >= 0) {
+            bc = b[c] - cmean[k];
+            b[c] = bc;
+        }
+        const double zz = bc * invd[c];
+        v[0] += bc * zz;
+        v[1] += zz * zz;
+        xv[c] = 0.0;
+        rv[c] = bc;
+    }
+    if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0())
+        set_cond(ctl, slot, start_inner(ctl, st, v[0], v[1]));
+}
+
+__global__ void k_cgS_dir(Dev g, const double* __restrict__ invd, const double* __restrict__ rv,
+                          double* __restrict__ pv, Ctl* ctl, const CgState* st) {
+    count_launch(ctl);
+    const double beta = st->first ? 0.0 : st->beta;
+    STREAM_LOOP(c, g.ncell) pv[c] = rv[c] * invd[c] + beta * pv[c];
+}
+
+__device__ __forceinline__ double face_inv_diag(const Dev& g, uint8_t f) {
+    return 1.0 / (double)(2 * g.d + (f >> 1));
+}
+
+__global__ void k_cgS_matvec(Dev g, const uint8_t* __restrict__ mask,
+                             const uint8_t* __restrict__ flags, const double* __restrict__ pv,
+                             double* __restrict__ qv, Ctl* ctl, CgState* st, double* partials,
+                             int slot) {
+    count_launch(ctl);
+    double v[1] = {0.0};
+    TILE_LOOP_BEGIN(g)
+        double out = 0.0;
+        if (mask[c] == 1) {
+            const double pc = pv[c];
+            for (int a = 0; a < g.d; ++a) {
+                int ex, ey, ez;
+                axis_step(a, 1, ex, ey, ez);
+                const uint8_t fl = flags[(long long)a * g.stride + c];
+                if (fl & 1) out += (pc - pv[cell_at(g, x - ex, y - ey, z - ez)]) * face_inv_diag(g, fl);
+                const long long cu = cell_at(g, x + ex, y + ey, z + ez);
+                if (cu >= 0) {
+                    const uint8_t fu = flags[(long long)a * g.stride + cu];
+                    if (fu & 1) out += (pc - pv[cu]) * face_inv_diag(g, fu);
+                }
+            }
+            v[0] += pc * out;
+        }
+        qv[c] = out;
+    TILE_LOOP_END
+    if (reduce_last_block<1>(v, partials, &ctl->ticket) && is_thread0()) {
+        const double dq = v[0];
+        if (!(dq > 0.0) || isinf(dq)) {
+            st->status = ST_BREAKDOWN;
+            st->alpha = 0.0;
+            set_cond(ctl, slot, 0u);
+        } else {
+            st->alpha = st->rho / dq;
+        }
+    }
+}
+
+__global__ void k_cgS_update(Dev g, const double* __restrict__ invd, double* __restrict__ xv,
+                             double* __restrict__ rv, const double* __restrict__ pv,
+                             const double* __restrict__ qv, Ctl* ctl, CgState* st,
+                             double* partials, int slot) {
+    count_launch(ctl);
+    const double alpha = st->alpha;
+    double v[2] = {0.0, 0.0};
+    STREAM_LOOP(c, g.ncell) {
+        xv[c] += alpha * pv[c];
+        const double r = rv[c] - alpha * qv[c];
+        rv[c] = r;
+        const double zz = r * invd[c];
+        v[0] += r * zz;
+        v[1] += zz * zz;
+    }
+    if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0())
+        set_cond(ctl, slot, finish_inner(ctl, st, v[0], v[1]));
+}
+
+// ------------------------------------------------------------------------------------
+// per-component means (nullspace of S-hat_simple and S: constants per fluid component)
+// ------------------------------------------------------------------------------------
+
+// Means of v over the (at most kMaxBig) big components, summed by the whole grid.
+__global__ void k_comp_big(Dev g, const int* __restrict__ cmp, const double* __restrict__ v,
+                           double* __restrict__ cmean, int nbig, Ctl* ctl,
+                           const CgState* outer, double* partials) {
+    count_launch(ctl);
+    if (outer->skip_next) return;
+    double s[kMaxBig];
+#pragma unroll
+    for (int b = 0; b < kMaxBig; ++b) s[b] = 0.0;
+    STREAM_LOOP(c, g.ncell) {
+        const int k = cmp[c];
+        if (k >= 0 && k < nbig) {
+            const double vc = v[c];
+#pragma unroll
+            for (int b = 0; b < kMaxBig; ++b) s[b] += (k == b) ? vc : 0.0;
+        }
+    }
+    if (reduce_last_block<kMaxBig>(s, partials, &ctl->ticket) && is_thread0()) {
+        for (int b = 0; b < nbig; ++b) cmean[b] = s[b] / ctl->big_size[b];
+    }
+}
+
+// Means of v over the small components, one warp per component (cells in fixed order).
+__global__ void k_comp_small(const int* __restrict__ start, const int* __restrict__ cells,
+                             const double* __restrict__ v, double* __restrict__ cmean, int nbig,
+                             int nsmall, Ctl* ctl, const CgState* outer) {
+    count_launch(ctl);
+    if (outer->skip_next) return;
+    const int lane = threadIdx.x & 31;
+    const int warps = blockDim.x >> 5;
+    for (long long j = (long long)blockIdx.x * warps + (threadIdx.x >> 5); j < nsmall;
+         j += (long long)gridDim.x * warps) {
+        const int b0 = start[j], b1 = start[j + 1];
+        double s = 0.0;
+        for (int i = b0 + lane; i < b1; i += 32) s += v[cells[i]];
+        s = warp_sum(s);
+        if (lane == 0) cmean[nbig + j] = s / (double)(b1 - b0);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// outer Schur CG (Algorithm 1), cell space, FP64
+// ------------------------------------------------------------------------------------
+
+// g = B u (u = A^-1 f); r = g, p = 0, d = g; zero-RHS test.
+__global__ void k_outer_init(Dev g, const uint8_t* __restrict__ mask, const uint8_t* __restrict__ flags,
+                             const double* __restrict__ u, double* __restrict__ gv,
+                             double* __restrict__ rv, double* __restrict__ pv,
+                             double* __restrict__ dv, Ctl* ctl, double* partials, int slot) {
+    count_launch(ctl);
+    double v[2] = {0.0, 0.0};
+    TILE_LOOP_BEGIN(g)
+        double gc = 0.0;
+        if (mask[c] == 1) {
+            double s = 0.0, sa = 0.0;
+            for (int a = 0; a < g.d; ++a) {
+                int ex, ey, ez;
+                axis_step(a, 1, ex, ey, ez);
+                const double up = face_val(g, flags, u, a, x + ex, y + ey, z + ez);
+                const double lo = face_val(g, flags, u, a, x, y, z);
+                s += up - lo;
+                sa += fabs(up) + fabs(lo);
+            }
+            gc = -g.hinv * s;
+            v[0] += gc * gc;
+            v[1] += (g.hinv * sa) * (g.hinv * sa);
+        }
+        gv[c] = gc;
+        rv[c] = gc;
+        pv[c] = 0.0;
+        dv[c] = gc;
+    TILE_LOOP_END
+    if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0()) {
+        ctl->g_norm2 = v[0];
+        ctl->g_scale2 = v[1];
+        const int zero = (v[0] == 0.0) || (sqrt(v[0]) <= kZeroRhsRtol * sqrt(v[1]));
+        ctl->zero_rhs = zero;
+        CgState* o = &ctl->out;
+        o->iter = 0;
+        o->status = ST_OK;
+        o->rr0 = v[0];
+        o->rho = v[0];
+        o->zz0 = v[0];
+        o->alpha = o->beta = 0.0;
+        o->done = zero;
+        o->skip_next = zero;
+        o->cap = 0;
+        o->rel = zero ? 0.0 : 1.0;
+        o->relz = zero ? 0.0 : 1.0;
+        set_cond(ctl, slot, zero ? 0u : 1u);
+    }
+}
+
+// SIMPLE: z_0 = S-hat^-1 r_0 minus its fluid mean; d = z_0, rho = r.z, ||z_0||^2.
+__global__ void k_outer_start(Dev g, const int* __restrict__ cmp, const double* __restrict__ cmean,
+                              const double* __restrict__ sx, const double* __restrict__ rv,
+                              double* __restrict__ dv, Ctl* ctl, double* partials, int slot) {
+    count_launch(ctl);
+    if (ctl->out.done) return;
+    double v[2] = {0.0, 0.0};
+    STREAM_LOOP(c, g.ncell) {
+        const int k = cmp[c];
+        const double zc = (k >= 0) ? sx[c] - cmean[k] : 0.0;
+        dv[c] = zc;
+        v[0] += rv[c] * zc;
+        v[1] += zc * zc;
+    }
+    if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0()) {
+        CgState* o = &ctl->out;
+        o->rho = v[0];
+        o->zz0 = v[1];
+        if (v[1] == 0.0) {
+            o->done = 1;
+            o->skip_next = 1;
+            o->relz = 0.0;
+            set_cond(ctl, slot, 0u);
+        }
+    }
+}
+
+// q = B u with u = A^-1 B^T d; alpha = rho / d.q.
+__global__ void k_outer_div(Dev g, const uint8_t* __restrict__ mask, const uint8_t* __restrict__ flags,
+                            const double* __restrict__ u, const double* __restrict__ dv,
+                            double* __restrict__ qv, Ctl* ctl, double* partials, int slot) {
+    count_launch(ctl);
+    double v[1] = {0.0};
+    TILE_LOOP_BEGIN(g)
+        double qc = 0.0;
+        if (mask[c] == 1) {
+            double s = 0.0;
+            for (int a = 0; a < g.d; ++a) {
+                int ex, ey, ez;
+                axis_step(a, 1, ex, ey, ez);
+                s += face_val(g, flags, u, a, x + ex, y + ey, z + ez) - face_val(g, flags, u, a, x, y, z);
+            }
+            qc = -g.hinv * s;
+            v[0] += dv[c] * qc;
+        }
+        qv[c] = qc;
+    TILE_LOOP_END
+    if (reduce_last_block<1>(v, partials, &ctl->ticket) && is_thread0()) {
+        CgState* o = &ctl->out;
+        const double dq = v[0];
+        if (!(dq > 0.0) || isinf(dq)) {
+            o->status = ST_BREAKDOWN;
+            o->alpha = 0.0;
+            o->done = 1;
+            o->skip_next = 1;
+            o->iter += 1;
+            set_cond(ctl, slot, 0u);
+        } else {
+            o->alpha = o->rho / dq;
+        }
+    }
+}
+
+// p += alpha d, r -= alpha q, ||r||; unpreconditioned test; Uzawa: beta.
+__global__ void k_outer_update(Dev g, double* __restrict__ pv, double* __restrict__ rv,
+                               const double* __restrict__ dv, const double* __restrict__ qv,
+                               Ctl* ctl, double* partials, int slot) {
+    count_launch(ctl);
+    CgState* o = &ctl->out;
+    if (o->done) return;
+    const double alpha = o->alpha;
+    double v[1] = {0.0};
+    STREAM_LOOP(c, g.ncell) {
+        pv[c] += alpha * dv[c];
+        const double r = rv[c] - alpha * qv[c];
+        rv[c] = r;
+        v[0] += r * r;
+    }
+    if (reduce_last_block<1>(v, partials, &ctl->ticket) && is_thread0()) {
+        o->iter += 1;
+        o->total += 1;
+        const double rel = sqrt(v[0] / o->rr0);
+        o->rel = rel;
+        unsigned cont = 1u;
+        if (ctl->stop_norm == 0 && rel < o->tol) {
+            o->status = ST_OK;
+            o->relz = nan("");
+            cont = 0u;
+        } else if (ctl->precond == 0) {
+            // Uzawa: z = r
+            o->relz = sqrt(v[0] / o->zz0);
+            if (ctl->stop_norm == 1 && o->relz < o->tol) {
+                o->status = ST_OK;
+                cont = 0u;
+            } else if (!(rel == rel)) {
+                o->status = ST_BREAKDOWN;
+                cont = 0u;
+            } else if (o->iter >= o->max_iter) {
+                o->status = ST_NOTCONV;
+                cont = 0u;
+            } else {
+                o->beta = v[0] / o->rho;
+                o->rho = v[0];
+            }
+        } else {
+            o->cap = (o->iter >= o->max_iter);
+            if (!(rel == rel)) {
+                o->status = ST_BREAKDOWN;
+                cont = 0u;
+            }
+        }
+        if (!cont) {
+            o->done = 1;
+            o->skip_next = 1;
+            set_cond(ctl, slot, 0u);
+        } else {
+            o->skip_next = 0;
+        }
+    }
+}
+
+// SIMPLE: z = S-hat^-1 r minus its fluid mean; rho' = r.z, ||z||; preconditioned test; beta.
+__global__ void k_outer_dots(Dev g, const int* __restrict__ cmp, const double* __restrict__ cmean,
+                             const double* __restrict__ sx, const double* __restrict__ rv,
+                             Ctl* ctl, double* partials, int slot) {
+    count_launch(ctl);
+    CgState* o = &ctl->out;
+    if (o->done) return;
+    double v[2] = {0.0, 0.0};
+    STREAM_LOOP(c, g.ncell) {
+        const int k = cmp[c];
+        const double zc = (k >= 0) ? sx[c] - cmean[k] : 0.0;
+        v[0] += rv[c] * zc;
+        v[1] += zc * zc;
+    }
+    if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0()) {
+        o->relz = sqrt(v[1] / o->zz0);
+        unsigned cont = 1u;
+        if (ctl->stop_norm == 1 && o->relz < o->tol) {
+            o->status = ST_OK;
+            cont = 0u;
+        } else if (o->cap) {
+            o->status = ST_NOTCONV;
+            cont = 0u;
+        } else {
+            o->beta = v[0] / o->rho;
+            o->rho = v[0];
+        }
+        if (!cont) {
+            o->done = 1;
+            set_cond(ctl, slot, 0u);
+        }
+    }
+}
+
+// d = z + beta d (Uzawa: z = r).
+__global__ void k_outer_dir(Dev g, const int* __restrict__ cmp, const double* __restrict__ cmean,
+                            const double* __restrict__ sx, const double* __restrict__ rv,
+                            double* __restrict__ dv, Ctl* ctl) {
+    count_launch(ctl);
+    const CgState* o = &ctl->out;
+    if (o->done) return;
+    const double beta = o->beta;
+    if (ctl->precond == 0) {
+        STREAM_LOOP(c, g.ncell) dv[c] = rv[c] + beta * dv[c];
+    } else {
+        STREAM_LOOP(c, g.ncell) {
+            const int k = cmp[c];
+            const double zc = (k >= 0) ? sx[c] - cmean[k] : 0.0;
+            dv[c] = zc + beta * dv[c];
+        }
+    }
+}
+
+// u = x (the recovered velocity) and the per-axis sums of u for the permeability.
+__global__ void k_copy_u(Dev g, const uint8_t* __restrict__ flags, const double* __restrict__ xv,
+                         double* __restrict__ u, Ctl* ctl, double* partials) {
+    count_launch(ctl);
+    double v[3] = {0.0, 0.0, 0.0};
+    const long long n = (long long)g.d * g.stride;
+    STREAM_LOOP(i, n) {
+        const double xi = (flags[i] & 1) ? xv[i] : 0.0;
+        u[i] = xi;
+        const int a = (int)(i / g.stride);
+        v[0] += (a == 0) ? xi : 0.0;
+        v[1] += (a == 1) ? xi : 0.0;
+        v[2] += (a == 2) ? xi : 0.0;
+    }
+    if (reduce_last_block<3>(v, partials, &ctl->ticket) && is_thread0()) {
+        for (int a = 0; a < 3; ++a) ctl->perm[a] = v[a] / (double)g.ncell;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// recorded control flow
+// ------------------------------------------------------------------------------------
+
+static inline dim3 tblock() { return dim3(kTileX, kTileY, 1); }
+static inline dim3 tgrid(const Handle& H) {
+    const long long gx = (H.g.nx + kTileX - 1) / kTileX, gy = (H.g.ny + kTileY - 1) / kTileY;
+    const long long nt = gx * gy * H.g.nz;
+    return dim3((unsigned)(nt < H.target_blocks ? nt : H.target_blocks));
+}
+static inline dim3 sgrid(const Handle& H, long long n) {
+    const long long nb = (n + kBlock - 1) / kBlock;
+    return dim3((unsigned)(nb < H.target_blocks ? (nb > 0 ? nb : 1) : H.target_blocks));
+}
+static inline dim3 sblock() { return dim3(kBlock); }
+
+// One inner A solve with the right-hand side already formed by k_cgA_init (slot s).
+static void record_A_loop(Handle& H, Recorder& R, CgState* st, int s) {
+    const long long nf = (long long)H.g.d * H.g.stride;
+    R.loop(s, [&, st, s, nf](Recorder& B) {
+        B.launch("cgA_dir", k_cgA_dir, sgrid(H, nf), sblock(), H.g, H.flags, H.ar, H.ap, H.dctl, st);
+        B.launch("cgA_matvec", k_cgA_matvec, tgrid(H), tblock(), H.g, H.flags, H.ap, H.aq, H.dctl,
+                 st, H.partials, s);
+        B.launch("cgA_update", k_cgA_update, sgrid(H, nf), sblock(), H.g, H.flags, H.ax, H.ar, H.ap,
+                 H.aq, H.dctl, st, H.partials, s);
+    });
+}
+
+// Slots are allocated before any loop body is recorded: in host-driven mode a body runs
+// once per iteration and must not allocate.
+static void record_comp_means(Handle& H, Recorder& R, const double* v) {
+    const CgState* outer = &H.dctl->out;
+    R.launch("comp_big", k_comp_big, sgrid(H, H.g.ncell), sblock(), H.g, (const int*)H.cmp, v,
+             H.cmean, H.n_big, H.dctl, outer, H.partials);
+    if (H.n_small > 0) {
+        const long long nb = (H.n_small + 7) / 8;
+        const dim3 grid((unsigned)(nb < H.target_blocks ? nb : H.target_blocks));
+        R.launch("comp_small", k_comp_small, grid, sblock(), (const int*)H.small_start,
+                 (const int*)H.small_cells, v, H.cmean, H.n_big, H.n_small, H.dctl, outer);
+    }
+}
+
+// z = S-hat^+ r: r is projected onto the range (per-component means removed, in place),
+// the inner CG runs, and the per-component means of the solution are left in cmean for
+// the consumers to subtract.
+static void record_S_solve(Handle& H, Recorder& R, int s) {
+    CgState* st = &H.dctl->inS;
+    record_comp_means(H, R, H.orr);
+    R.launch("cgS_init", k_cgS_init, sgrid(H, H.g.ncell), sblock(), H.g, (const double*)H.invdS,
+             (const int*)H.cmp, (const double*)H.cmean, H.orr, H.sx, H.sr, H.dctl, st,
+             (const CgState*)&H.dctl->out, H.partials, s);
+    R.loop(s, [&, st, s](Recorder& B) {
+        B.launch("cgS_dir", k_cgS_dir, sgrid(H, H.g.ncell), sblock(), H.g, (const double*)H.invdS,
+                 (const double*)H.sr, H.sp, H.dctl, (const CgState*)st);
+        B.launch("cgS_matvec", k_cgS_matvec, tgrid(H), tblock(), H.g, H.mask, H.flags,
+                 (const double*)H.sp, H.sq, H.dctl, st, H.partials, s);
+        B.launch("cgS_update", k_cgS_update, sgrid(H, H.g.ncell), sblock(), H.g,
+                 (const double*)H.invdS, H.sx, H.sr, (const double*)H.sp, (const double*)H.sq,
+                 H.dctl, st, H.partials, s);
+    });
+}
+
+void record_solve(Handle& H, Recorder& R, int precond) {
+    Ctl* ctl = H.dctl;
+    CgState* inA = &ctl->inA;
+    // g = B A^-1 f
+    const int s_rhs = R.new_slot();
+    const int s_out = R.new_slot();
+    const int s_s0 = R.new_slot();
+    const int s_a = R.new_slot();
+    const int s_s = R.new_slot();
+    R.launch("cgA_init", k_cgA_init, tgrid(H), tblock(), H.g, H.flags, H.ax, H.ar,
+             (const double*)nullptr, 0.0, 1.0, (const double*)nullptr, ctl, inA, H.partials, s_rhs);
+    record_A_loop(H, R, inA, s_rhs);
+    R.launch("outer_init", k_outer_init, tgrid(H), tblock(), H.g, H.mask, H.flags,
+             (const double*)H.ax, H.og, H.orr, H.op, H.od, ctl, H.partials, s_out);
+    if (precond == 1) {
+        record_S_solve(H, R, s_s0);
+        R.launch("outer_start", k_outer_start, sgrid(H, H.g.ncell), sblock(), H.g,
+                 (const int*)H.cmp, (const double*)H.cmean, (const double*)H.sx,
+                 (const double*)H.orr, H.od, ctl, H.partials, s_out);
+    }
+    R.loop(s_out, [&, ctl, inA, precond, s_out, s_a, s_s](Recorder& B) {
+        // q = S d = B A^-1 B^T d
+        B.launch("cgA_init", k_cgA_init, tgrid(H), tblock(), H.g, H.flags, H.ax, H.ar,
+                 (const double*)H.od, 1.0, 0.0, (const double*)nullptr, ctl, inA, H.partials, s_a);
+        record_A_loop(H, B, inA, s_a);
+        B.launch("outer_div", k_outer_div, tgrid(H), tblock(), H.g, H.mask, H.flags,
+                 (const double*)H.ax, (const double*)H.od, H.oq, ctl, H.partials, s_out);
+        B.launch("outer_update", k_outer_update, sgrid(H, H.g.ncell), sblock(), H.g, H.op, H.orr,
+                 (const double*)H.od, (const double*)H.oq, ctl, H.partials, s_out);
+        if (precond == 1) {
+            record_S_solve(H, B, s_s);
+            B.launch("outer_dots", k_outer_dots, sgrid(H, H.g.ncell), sblock(), H.g,
+                     (const int*)H.cmp, (const double*)H.cmean, (const double*)H.sx,
+                     (const double*)H.orr, ctl, H.partials, s_out);
+        }
+        B.launch("outer_dir", k_outer_dir, sgrid(H, H.g.ncell), sblock(), H.g, (const int*)H.cmp,
+                 (const double*)H.cmean, (const double*)H.sx, (const double*)H.orr, H.od, ctl);
+    });
+}
+
+void record_recover(Handle& H, Recorder& R) {
+    Ctl* ctl = H.dctl;
+    CgState* inA = &ctl->inA;
+    const int s = R.new_slot();
+    R.launch("cgA_init", k_cgA_init, tgrid(H), tblock(), H.g, H.flags, H.ax, H.ar,
+             (const double*)H.op, -1.0, 1.0, (const double*)nullptr, ctl, inA, H.partials, s);
+    record_A_loop(H, R, inA, s);
+    const long long nf = (long long)H.g.d * H.g.stride;
+    R.launch("copy_u", k_copy_u, sgrid(H, nf), sblock(), H.g, H.flags, (const double*)H.ax, H.u,
+             ctl, H.partials);
+}
+
+void record_solve_A(Handle& H, Recorder& R, const double* b, double* x) {
+    Ctl* ctl = H.dctl;
+    CgState* st = &ctl->solo;
+    const int s = R.new_slot();
+    R.launch("cgA_init", k_cgA_init, tgrid(H), tblock(), H.g, H.flags, H.ax, H.ar,
+             (const double*)nullptr, 0.0, 0.0, b, ctl, st, H.partials, s);
+    record_A_loop(H, R, st, s);
+    (void)x;
+}
+
+// One launch of a hot kernel on the handle's stream between two CUDA events (the
+// kernels read and write the solver's own buffers; the solo CG state absorbs the scalars).
+cudaError_t time_kernel(Handle& H, int which, int slot, float* ms) {
+    if (!H.ev0) {
+        cudaError_t e = cudaEventCreate(&H.ev0);
+        if (e == cudaSuccess) e = cudaEventCreate(&H.ev1);
+        if (e != cudaSuccess) return e;
+    }
+    Ctl* ctl = H.dctl;
+    CgState* st = &ctl->solo;
+    const long long nf = (long long)H.g.d * H.g.stride;
+    cudaError_t e = cudaEventRecord(H.ev0, H.stream);
+    if (e != cudaSuccess) return e;
+    switch (which) {
+        case 0:
+            k_cgA_dir<<<sgrid(H, nf), sblock(), 0, H.stream>>>(H.g, H.flags, H.ar, H.ap, ctl, st);
+            break;
+        case 1:
+            k_cgA_matvec<<<tgrid(H), tblock(), 0, H.stream>>>(H.g, H.flags, H.ap, H.aq, ctl, st,
+                                                              H.partials, slot);
+            break;
+        case 2:
+            k_cgA_update<<<sgrid(H, nf), sblock(), 0, H.stream>>>(H.g, H.flags, H.ax, H.ar, H.ap,
+                                                                  H.aq, ctl, st, H.partials, slot);
+            break;
+        case 3:
+            k_cgS_dir<<<sgrid(H, H.g.ncell), sblock(), 0, H.stream>>>(H.g, H.invdS, H.sr, H.sp,
+                                                                      ctl, st);
+            break;
+        case 4:
+            k_cgS_matvec<<<tgrid(H), tblock(), 0, H.stream>>>(H.g, H.mask, H.flags, H.sp, H.sq,
+                                                              ctl, st, H.partials, slot);
+            break;
+        case 5:
+            k_cgS_update<<<sgrid(H, H.g.ncell), sblock(), 0, H.stream>>>(
+                H.g, H.invdS, H.sx, H.sr, H.sp, H.sq, ctl, st, H.partials, slot);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(H.ev1, H.stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(H.ev1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, H.ev0, H.ev1);
+    return e;
+}
+
+}  // namespace schur

@@ -1,0 +1,80 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every declared symbol,
+and the ctypes structures match the C header layout.  No GPU call is made."""
+
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2307_05266_gb300 import _build, binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "schur.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return binding.load(build_if_missing=False)
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(schur_[a-z_A-Z0-9]+)\s*\(", text)))
+
+
+def test_header_declares_binding_names():
+    assert declared_functions() == sorted(binding.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_struct_layouts_match_header():
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "schur.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(schur_opts), sizeof(schur_stats),
+         sizeof(schur_geom_info), offsetof(schur_opts, tol), offsetof(schur_stats, g_norm),
+         offsetof(schur_geom_info, device_bytes));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as td:
+        c = os.path.join(td, "l.c")
+        exe = os.path.join(td, "l")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        vals = [int(v) for v in subprocess.check_output([exe]).split()]
+    got = [ctypes.sizeof(binding.Opts), ctypes.sizeof(binding.Stats),
+           ctypes.sizeof(binding.GeomInfo), binding.Opts.tol.offset,
+           binding.Stats.g_norm.offset, binding.GeomInfo.device_bytes.offset]
+    assert vals == got
+
+
+def test_defaults(lib):
+    o = binding.default_opts()
+    assert o.precond == binding.SIMPLE and o.stop_norm == binding.STOP_UNPRECOND
+    assert o.tol == 1e-8 and o.tol_inner_A == 1e-12 and o.max_inner == 20000
+
+
+def test_null_arguments_rejected_without_gpu(lib):
+    out = ctypes.c_void_p()
+    dims = (ctypes.c_int64 * 3)(4, 4, 4)
+    per = (ctypes.c_int * 3)(1, 1, 1)
+    assert lib.schur_create_geometry(None, 3, dims, per, None, ctypes.byref(out)) == binding.SCHUR_EINVAL
+    m = (ctypes.c_uint8 * 64)()
+    assert lib.schur_create_geometry(m, 4, dims, per, None, ctypes.byref(out)) == binding.SCHUR_EINVAL
+    dims1 = (ctypes.c_int64 * 3)(1, 4, 4)
+    assert lib.schur_create_geometry(m, 3, dims1, per, None, ctypes.byref(out)) == binding.SCHUR_EINVAL
+    assert b"extent" in lib.schur_last_error()
+    assert lib.schur_solve(None, None, None) == binding.SCHUR_EINVAL
+    lib.schur_destroy(None)

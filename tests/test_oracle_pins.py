@@ -213,8 +213,10 @@ def test_cg_solution_equals_dense_min_norm(shape, phi, seed, periodic, precond):
     mask = _random_mask(shape, phi, seed)
     d = len(shape)
     f = (1.0,) + (0.0,) * (d - 1)
-    r = stokes.solve(mask, f, stokes.Options(precond=precond, tol=1e-11,
-                                             max_outer=500), periodic)
+    # SIMPLE stalls near 1e-9 with 1e-12 inner solves (inexact preconditioner)
+    tol = 1e-11 if precond == stokes.UZAWA else 1e-9
+    r = stokes.solve(mask, f, stokes.Options(precond=precond, tol=tol, max_outer=500),
+                     periodic)
     prob = r["problem"]
     S = dense.schur_dense(prob)
     A = prob.A.toarray()
@@ -255,7 +257,7 @@ def test_pcg_finite_termination():
 def test_recovered_velocity_divergence_free():
     """A u = f - B^T p with S p = g makes B u = 0 up to the solver tolerances."""
     m = synth.sphere_packing(16, 3, 5, 0.45, seed=1)
-    r = stokes.solve(m, (0.0, 0.0, 1.0), stokes.Options(precond=stokes.SIMPLE, tol=1e-10))
+    r = stokes.solve(m, (0.0, 0.0, 1.0), stokes.Options(precond=stokes.SIMPLE, tol=1e-9))
     prob = r["problem"]
     div = prob.B @ r["u"]
     assert np.linalg.norm(div) <= 1e-8 * np.linalg.norm(abs(prob.B) @ np.abs(r["u"]))
@@ -263,7 +265,7 @@ def test_recovered_velocity_divergence_free():
 
 def test_both_preconditioners_agree():
     m = synth.sphere_packing(16, 3, 5, 0.4, seed=4)
-    ks = [stokes.solve(m, (1.0, 0, 0), stokes.Options(precond=p, tol=1e-10))["k"][0]
+    ks = [stokes.solve(m, (1.0, 0, 0), stokes.Options(precond=p, tol=1e-9))["k"][0]
           for p in (stokes.UZAWA, stokes.SIMPLE)]
     assert abs(ks[0] - ks[1]) <= 1e-8 * abs(ks[0])
 
