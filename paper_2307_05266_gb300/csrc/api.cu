@@ -62,7 +62,7 @@ void free_all(Handle& H) {
     H.graph_recover = H.graph_solo = nullptr;
     void* bufs[] = {H.mask, H.flags, H.invdS, H.ax, H.ar, H.ap, H.aq, H.sx, H.sr, H.sp,
                     H.sq, H.op, H.orr, H.od, H.oq, H.og, H.u, H.partials, H.dctl,
-                    H.cmp, H.cmean, H.small_start, H.small_cells};
+                    H.cmp, H.cmean, H.small_start, H.small_cells, H.ulist, H.flist};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (H.hctl) cudaFreeHost(H.hctl);
@@ -150,6 +150,26 @@ int build_components(Handle& H, const uint8_t* m) {
     std::vector<int> fill(start.begin(), start.end() - 1);
     for (long long c = 0; c < n; ++c)
         if (comp[c] >= nbig) cells[fill[comp[c] - nbig]++] = (int)c;
+    // compact work lists: unknown faces (both cells fluid) and fluid cells, ascending
+    std::vector<uint32_t> ul, fl;
+    for (int a = 0; a < g.d; ++a)
+        for (int z = 0; z < g.nz; ++z)
+            for (int y = 0; y < g.ny; ++y)
+                for (int x = 0; x < g.nx; ++x) {
+                    const long long c = ((long long)z * g.ny + y) * g.nx + x;
+                    if (m[c] != 1) continue;
+                    if (a == 0) fl.push_back((uint32_t)c);
+                    int lx = x - (a == 0), ly = y - (a == 1), lz = z - (a == 2);
+                    if (lx < 0) { if (!g.per[0]) continue; lx += g.nx; }
+                    if (ly < 0) { if (!g.per[1]) continue; ly += g.ny; }
+                    if (lz < 0) { if (!g.per[2]) continue; lz += g.nz; }
+                    const long long l = ((long long)lz * g.ny + ly) * g.nx + lx;
+                    if (m[l] == 1) ul.push_back((uint32_t)(a * g.stride + c));
+                }
+    H.n_u = (long long)ul.size();
+    H.n_p = (long long)fl.size();
+    if (ul.empty()) ul.push_back(0);
+    if (fl.empty()) fl.push_back(0);
     H.n_comp = ncomp;
     H.n_big = nbig;
     H.n_small = nsmall;
@@ -164,6 +184,14 @@ int build_components(Handle& H, const uint8_t* m) {
                             cudaMemcpyHostToDevice, H.stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(H.small_cells, cells.data(), cells.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, H.stream);
+    if (e == cudaSuccess) e = alloc(H, &H.ulist, ul.size());
+    if (e == cudaSuccess) e = alloc(H, &H.flist, fl.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(H.ulist, ul.data(), ul.size() * sizeof(uint32_t),
+                            cudaMemcpyHostToDevice, H.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(H.flist, fl.data(), fl.size() * sizeof(uint32_t),
                             cudaMemcpyHostToDevice, H.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(H.stream);  // host vectors go out of scope
     if (e == cudaErrorMemoryAllocation) return set_error(SCHUR_ENOMEM, "device allocation failed");
@@ -247,7 +275,8 @@ int schur_create_geometry(const uint8_t* mask, int ndim, const int64_t dims[3],
             return set_error(SCHUR_EINVAL, "every extent must lie in [2, 2^20]");
     const long long nz = ndim == 3 ? dims[2] : 1;
     const long long ncell = dims[0] * dims[1] * nz;
-    if (ncell > 2147483647ll) return set_error(SCHUR_EINVAL, "grid too large (cells >= 2^31)");
+    if (ncell > 1400000000ll)  // 32-bit work-list entries over [d][stride]
+        return set_error(SCHUR_EINVAL, "grid too large (more than 1.4e9 cells)");
 
     schur_geom* G = new schur_geom();
     Handle& H = G->H;
@@ -266,6 +295,10 @@ int schur_create_geometry(const uint8_t* mask, int ndim, const int64_t dims[3],
     g.hinv = (double)g.nx;
     g.h2 = g.h * g.h;
     g.h2inv = g.hinv * g.hinv;
+    for (int k = 0; k < 5; ++k) {
+        g.diag[k] = (double)(2 * ndim + k);
+        g.wdiag[k] = 1.0 / g.diag[k];
+    }
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -554,6 +587,8 @@ int schur_solve_A(schur_geom_t G, const double* b, double* x, double tol, int ma
     CUDA_TRY(cudaGraphLaunch(H.exec_solo, H.stream), "cudaGraphLaunch");
     CUDA_TRY(cudaMemcpyAsync(x, H.ax, nf * sizeof(double), cudaMemcpyDeviceToDevice, H.stream),
              "copy solution");
+    // the staging buffer held caller values off the unknowns: restore the zero invariant
+    CUDA_TRY(cudaMemsetAsync(H.aq, 0, nf * sizeof(double), H.stream), "clear staging");
     if ((rc = download(H))) return rc;
     if (iters) *iters = c->solo.iter;
     const int st = map_status(c->solo.status);

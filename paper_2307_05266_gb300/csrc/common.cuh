@@ -36,7 +36,20 @@ struct Dev {
     long long ncell;
     long long stride;
     double h, hinv, h2inv, h2;
+    // tables indexed by the ghost count g = 0..4 of a face (GB300 has little FP64
+    // throughput, so no FP64 division or conversion appears in the hot loops)
+    double diag[5];   // 2d + g: diagonal of the dimensionless operator h^2 A
+    double wdiag[5];  // 1 / (2d + g)
 };
+
+__device__ __forceinline__ double tab5(const double (&t)[5], int k) {
+    double v = t[0];
+    v = (k == 1) ? t[1] : v;
+    v = (k == 2) ? t[2] : v;
+    v = (k == 3) ? t[3] : v;
+    v = (k == 4) ? t[4] : v;
+    return v;
+}
 
 // One Krylov instance (inner A solve, inner SIMPLE solve, outer Schur CG).
 struct CgState {

@@ -34,6 +34,10 @@ struct Handle {
     int* small_start = nullptr;  // [n_small + 1] CSR offsets of the small components
     int* small_cells = nullptr;  // cells of the small components, increasing per component
     int n_comp = 0, n_big = 0, n_small = 0;
+    // compact work lists (ascending): unknown faces (index into [d][stride]), fluid cells
+    uint32_t* ulist = nullptr;
+    uint32_t* flist = nullptr;
+    long long n_u = 0, n_p = 0;
     double* partials = nullptr;  // reduction scratch
     Ctl* dctl = nullptr;         // device control block
     Ctl* hctl = nullptr;         // pinned host shadow

@@ -39,10 +39,6 @@ namespace schur {
 
 __device__ __forceinline__ bool is_thread0() { return threadIdx.x == 0 && threadIdx.y == 0; }
 
-__device__ __forceinline__ double jac_A(const Dev& g, uint8_t f) {
-    // inverse of diag(A)_f = h^-2 (2d + g_f)
-    return g.h2 / (double)(2 * g.d + (f >> 1));
-}
 
 __device__ __forceinline__ double face_val(const Dev& g, const uint8_t* __restrict__ flags,
                                            const double* __restrict__ u, int a, int x, int y,
@@ -92,6 +88,81 @@ __device__ __forceinline__ unsigned start_inner(Ctl* ctl, CgState* st, double rz
 }
 
 // ------------------------------------------------------------------------------------
+// access patterns
+// ------------------------------------------------------------------------------------
+// Streaming kernels: a warp owns kU chunks of 32 consecutive elements per step (lane l
+// touches base + l + 32 j), so every load instruction is one coalesced 256-byte row and
+// each thread has kU independent loads in flight.  Loads and stores are predicated on
+// the face flag / cell mask: faces that are not unknowns and solid cells hold 0 in every
+// solver vector from allocation on and are never read or written, so HBM sectors that
+// hold no unknown are not touched.
+// Stencil kernels: a block owns a 32 x 8 tile of one component (or of the cells) and
+// marches along z over a chunk of planes; the x/y neighbour offsets (with periodic
+// wrap) are fixed per thread and computed once.
+constexpr int kU = 4;
+
+#define WARP_STREAM_BEGIN(n)                                                              \
+    {                                                                                     \
+        const long long lane_ = threadIdx.x & 31;                                         \
+        const long long nw_ = ((long long)gridDim.x * blockDim.x) >> 5;                   \
+        for (long long base_ = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5)  \
+                               * (32 * kU);                                               \
+             base_ < (n); base_ += nw_ * (32 * kU)) {                                     \
+            long long idx[kU];                                                            \
+            _Pragma("unroll") for (int j = 0; j < kU; ++j) idx[j] = base_ + lane_ + 32 * j;
+#define WARP_STREAM_END \
+        }               \
+    }
+
+// Per-thread neighbour offsets of a stencil column (x, y fixed, z marching).
+struct Nbr {
+    long long xm, xp, ym, yp;   // offsets to the x-1, x+1, y-1, y+1 cells
+    bool vxm, vxp, vym, vyp;    // false outside a closed box
+};
+
+__device__ __forceinline__ Nbr column_nbr(const Dev& g, int x, int y) {
+    Nbr n;
+    n.vxm = n.vxp = n.vym = n.vyp = true;
+    n.xm = -1; n.xp = 1;
+    n.ym = -(long long)g.nx; n.yp = g.nx;
+    if (x == 0) { if (g.per[0]) n.xm = g.nx - 1; else n.vxm = false; }
+    if (x == g.nx - 1) { if (g.per[0]) n.xp = -(long long)(g.nx - 1); else n.vxp = false; }
+    if (y == 0) { if (g.per[1]) n.ym = (long long)(g.ny - 1) * g.nx; else n.vym = false; }
+    if (y == g.ny - 1) { if (g.per[1]) n.yp = -(long long)(g.ny - 1) * g.nx; else n.vyp = false; }
+    return n;
+}
+
+// z offsets of plane z (periodic wrap or closed)
+__device__ __forceinline__ void z_nbr(const Dev& g, int z, long long plane, long long& zm,
+                                      long long& zp, bool& vzm, bool& vzp) {
+    zm = -plane; zp = plane; vzm = vzp = true;
+    if (z == 0) { if (g.per[2]) zm = (long long)(g.nz - 1) * plane; else vzm = false; }
+    if (z == g.nz - 1) { if (g.per[2]) zp = -(long long)(g.nz - 1) * plane; else vzp = false; }
+}
+
+// Grid of the stencil kernels: x-y tiles strided over blockIdx.x, gridDim.y = z chunks,
+// gridDim.z = field count (d components or 1 for cells).
+#define COLUMN_TILES_BEGIN(g)                                                         \
+    const int gx_ = ((g).nx + kTileX - 1) / kTileX;                                   \
+    const int gy_ = ((g).ny + kTileY - 1) / kTileY;                                   \
+    const int zc_ = ((g).nz + gridDim.y - 1) / gridDim.y;                             \
+    const int z0_ = blockIdx.y * zc_;                                                 \
+    const int z1_ = min((g).nz, z0_ + zc_);                                           \
+    const long long plane = (long long)(g).nx * (g).ny;                               \
+    for (int t_ = blockIdx.x; t_ < gx_ * gy_; t_ += gridDim.x) {                      \
+        const int x = (t_ % gx_) * kTileX + (int)threadIdx.x;                         \
+        const int y = (t_ / gx_) * kTileY + (int)threadIdx.y;                         \
+        if (x < (g).nx && y < (g).ny) {                                               \
+            const Nbr nb = column_nbr(g, x, y);                                       \
+            const long long cxy = (long long)y * (g).nx + x;                          \
+            for (int z = z0_; z < z1_; ++z) {                                         \
+                const long long c = z * plane + cxy;
+#define COLUMN_TILES_END \
+            }            \
+        }                \
+    }
+
+// ------------------------------------------------------------------------------------
 // inner CG on A (face space)
 // ------------------------------------------------------------------------------------
 
@@ -102,66 +173,107 @@ __global__ void k_cgA_init(Dev g, const uint8_t* __restrict__ flags, double* __r
                            double* partials, int slot) {
     count_launch(ctl);
     double v[2] = {0.0, 0.0};
-    TILE_LOOP_BEGIN(g)
-        for (int a = 0; a < g.d; ++a) {
+    const int a = blockIdx.z;
+    const uint8_t* F = flags + (long long)a * g.stride;
+    const long long lower = a == 0 ? 1 : (a == 1 ? g.nx : (long long)g.nx * g.ny);
+    const double fa = cf * ctl->f[a];
+    COLUMN_TILES_BEGIN(g)
+        const uint8_t f = F[c];
+        if (f & 1) {
+            // an unknown face has a fluid lower cell inside the box (wrap when periodic)
+            long long cl = c - lower;
+            if ((a == 0 && x == 0) || (a == 1 && y == 0) || (a == 2 && z == 0))
+                cl += (a == 0 ? g.nx : (a == 1 ? (long long)g.ny * g.nx : (long long)g.nz * plane));
+            double b = fa;
+            if (P) b += cp * (g.hinv * (P[c] - P[cl]));
             const long long i = (long long)a * g.stride + c;
-            const uint8_t f = flags[i];
-            double b = 0.0;
-            if (f & 1) {
-                b = cf * ctl->f[a];
-                if (P) {
-                    int ex, ey, ez;
-                    axis_step(a, 1, ex, ey, ez);
-                    b += cp * (g.hinv * (P[c] - P[cell_at(g, x - ex, y - ey, z - ez)]));
-                }
-                if (bvec) b += bvec[i];
-                const double zz = b * jac_A(g, f);
-                v[0] += b * zz;
-                v[1] += zz * zz;
-            }
+            if (bvec) b += bvec[i];
+            b *= g.h2;  // right-hand side of the dimensionless system h^2 A x = h^2 b
+            const double zz = b * tab5(g.wdiag, f >> 1);
+            v[0] += b * zz;
+            v[1] += zz * zz;
             xv[i] = 0.0;
             rv[i] = b;
         }
-    TILE_LOOP_END
+    COLUMN_TILES_END
     if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0())
         set_cond(ctl, slot, start_inner(ctl, st, v[0], v[1]));
 }
 
-__global__ void k_cgA_dir(Dev g, const uint8_t* __restrict__ flags, const double* __restrict__ rv,
+// The inner A solve works with the dimensionless operator A' = h^2 A (diagonal 2d + g,
+// off-diagonal -1) and M' = diag(A'), right-hand side h^2 b: alpha, beta and every
+// iterate x are those of CG on A x = b with Jacobi M = diag(A), without the h^-2 factors.
+
+// Decode a face index of [d][stride] into component and cell coordinates.
+struct FaceAt {
+    int a, x, y, z;
+    long long c;
+};
+__device__ __forceinline__ FaceAt decode_face(const Dev& g, uint32_t i) {
+    FaceAt r;
+    const uint32_t s = (uint32_t)g.stride;
+    r.a = (i >= s) + (i >= 2u * s);
+    const uint32_t c = i - (uint32_t)r.a * s;
+    const uint32_t plane = (uint32_t)g.nx * (uint32_t)g.ny;
+    r.z = (int)(c / plane);
+    const uint32_t rem = c - (uint32_t)r.z * plane;
+    r.y = (int)(rem / (uint32_t)g.nx);
+    r.x = (int)(rem - (uint32_t)r.y * (uint32_t)g.nx);
+    r.c = c;
+    return r;
+}
+
+// p = M'^-1 r + beta p over the unknown-face list.
+__global__ void k_cgA_dir(Dev g, const uint32_t* __restrict__ list, long long n,
+                          const uint8_t* __restrict__ flags, const double* __restrict__ rv,
                           double* __restrict__ pv, Ctl* ctl, const CgState* st) {
     count_launch(ctl);
     const double beta = st->first ? 0.0 : st->beta;
-    const long long n = (long long)g.d * g.stride;
-    STREAM_LOOP(i, n) {
-        const uint8_t f = flags[i];
-        double out = 0.0;
-        if (f & 1) out = rv[i] * jac_A(g, f) + beta * pv[i];
-        pv[i] = out;
-    }
+    WARP_STREAM_BEGIN(n)
+        uint32_t i[kU];
+        int gh[kU];
+        double r[kU], p[kU];
+#pragma unroll
+        for (int j = 0; j < kU; ++j) i[j] = idx[j] < n ? list[idx[j]] : 0u;
+#pragma unroll
+        for (int j = 0; j < kU; ++j)
+            if (idx[j] < n) { gh[j] = flags[i[j]] >> 1; r[j] = rv[i[j]]; p[j] = pv[i[j]]; }
+#pragma unroll
+        for (int j = 0; j < kU; ++j)
+            if (idx[j] < n) pv[i[j]] = r[j] * tab5(g.wdiag, gh[j]) + beta * p[j];
+    WARP_STREAM_END
 }
 
-__global__ void k_cgA_matvec(Dev g, const uint8_t* __restrict__ flags, const double* __restrict__ pv,
+// q = A' p and p.q over the unknown-face list; neighbours that are not unknowns hold 0.
+__global__ void k_cgA_matvec(Dev g, const uint32_t* __restrict__ list, long long n,
+                             const uint8_t* __restrict__ flags, const double* __restrict__ pv,
                              double* __restrict__ qv, Ctl* ctl, CgState* st, double* partials,
                              int slot) {
     count_launch(ctl);
     double v[1] = {0.0};
-    TILE_LOOP_BEGIN(g)
-        for (int a = 0; a < g.d; ++a) {
-            const long long i = (long long)a * g.stride + c;
-            const uint8_t f = flags[i];
-            double out = 0.0;
-            if (f & 1) {
-                double s = face_val(g, flags, pv, a, x - 1, y, z) + face_val(g, flags, pv, a, x + 1, y, z);
-                s += face_val(g, flags, pv, a, x, y - 1, z) + face_val(g, flags, pv, a, x, y + 1, z);
-                if (g.d == 3)
-                    s += face_val(g, flags, pv, a, x, y, z - 1) + face_val(g, flags, pv, a, x, y, z + 1);
-                const double pc = pv[i];
-                out = g.h2inv * ((double)(2 * g.d + (f >> 1)) * pc - s);
-                v[0] += pc * out;
-            }
-            qv[i] = out;
+    const long long plane = (long long)g.nx * g.ny;
+    STREAM_LOOP(k, n) {
+        const uint32_t i = list[k];
+        const FaceAt f = decode_face(g, i);
+        const int gh = flags[i] >> 1;
+        const double* P = pv + (long long)f.a * g.stride;
+        const long long c = f.c;
+        const double pc = P[c];
+        const long long xm = f.x > 0 ? c - 1 : (g.per[0] ? c + g.nx - 1 : -1);
+        const long long xp = f.x < g.nx - 1 ? c + 1 : (g.per[0] ? c - (g.nx - 1) : -1);
+        const long long ym = f.y > 0 ? c - g.nx : (g.per[1] ? c + (long long)(g.ny - 1) * g.nx : -1);
+        const long long yp = f.y < g.ny - 1 ? c + g.nx : (g.per[1] ? c - (long long)(g.ny - 1) * g.nx : -1);
+        double s = (xm >= 0 ? P[xm] : 0.0) + (xp >= 0 ? P[xp] : 0.0);
+        s += (ym >= 0 ? P[ym] : 0.0) + (yp >= 0 ? P[yp] : 0.0);
+        if (g.d == 3) {
+            const long long zm = f.z > 0 ? c - plane : (g.per[2] ? c + (long long)(g.nz - 1) * plane : -1);
+            const long long zp = f.z < g.nz - 1 ? c + plane : (g.per[2] ? c - (long long)(g.nz - 1) * plane : -1);
+            s += (zm >= 0 ? P[zm] : 0.0) + (zp >= 0 ? P[zp] : 0.0);
         }
-    TILE_LOOP_END
+        const double out = tab5(g.diag, gh) * pc - s;
+        qv[i] = out;
+        v[0] += pc * out;
+    }
     if (reduce_last_block<1>(v, partials, &ctl->ticket) && is_thread0()) {
         const double dq = v[0];
         if (!(dq > 0.0) || isinf(dq)) {
@@ -174,25 +286,41 @@ __global__ void k_cgA_matvec(Dev g, const uint8_t* __restrict__ flags, const dou
     }
 }
 
-__global__ void k_cgA_update(Dev g, const uint8_t* __restrict__ flags, double* __restrict__ xv,
+// x += alpha p, r -= alpha q; r.z and z.z (z = M'^-1 r) over the unknown-face list.
+__global__ void k_cgA_update(Dev g, const uint32_t* __restrict__ list, long long n,
+                             const uint8_t* __restrict__ flags, double* __restrict__ xv,
                              double* __restrict__ rv, const double* __restrict__ pv,
                              const double* __restrict__ qv, Ctl* ctl, CgState* st,
                              double* partials, int slot) {
     count_launch(ctl);
     const double alpha = st->alpha;
     double v[2] = {0.0, 0.0};
-    const long long n = (long long)g.d * g.stride;
-    STREAM_LOOP(i, n) {
-        const uint8_t f = flags[i];
-        if (f & 1) {
-            xv[i] += alpha * pv[i];
-            const double r = rv[i] - alpha * qv[i];
-            rv[i] = r;
-            const double zz = r * jac_A(g, f);
-            v[0] += r * zz;
-            v[1] += zz * zz;
-        }
-    }
+    WARP_STREAM_BEGIN(n)
+        uint32_t i[kU];
+        int gh[kU];
+        double xx[kU], p[kU], r[kU], q[kU];
+#pragma unroll
+        for (int j = 0; j < kU; ++j) i[j] = idx[j] < n ? list[idx[j]] : 0u;
+#pragma unroll
+        for (int j = 0; j < kU; ++j)
+            if (idx[j] < n) {
+                gh[j] = flags[i[j]] >> 1;
+                xx[j] = xv[i[j]];
+                p[j] = pv[i[j]];
+                r[j] = rv[i[j]];
+                q[j] = qv[i[j]];
+            }
+#pragma unroll
+        for (int j = 0; j < kU; ++j)
+            if (idx[j] < n) {
+                xv[i[j]] = xx[j] + alpha * p[j];
+                const double rn = r[j] - alpha * q[j];
+                rv[i[j]] = rn;
+                const double zz = rn * tab5(g.wdiag, gh[j]);
+                v[0] += rn * zz;
+                v[1] += zz * zz;
+            }
+    WARP_STREAM_END
     if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0())
         set_cond(ctl, slot, finish_inner(ctl, st, v[0], v[1]));
 }
@@ -215,57 +343,76 @@ __global__ void k_cgS_init(Dev g, const double* __restrict__ invd, const int* __
     double v[2] = {0.0, 0.0};
     STREAM_LOOP(c, g.ncell) {
         const int k = cmp[c];
-        double bc = 0.0;
         if (k >= 0) {
-            bc = b[c] - cmean[k];
+            const double bc = b[c] - cmean[k];
             b[c] = bc;
+            const double zz = bc * invd[c];
+            v[0] += bc * zz;
+            v[1] += zz * zz;
+            xv[c] = 0.0;
+            rv[c] = bc;
         }
-        const double zz = bc * invd[c];
-        v[0] += bc * zz;
-        v[1] += zz * zz;
-        xv[c] = 0.0;
-        rv[c] = bc;
     }
     if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0())
         set_cond(ctl, slot, start_inner(ctl, st, v[0], v[1]));
 }
 
-__global__ void k_cgS_dir(Dev g, const double* __restrict__ invd, const double* __restrict__ rv,
+__global__ void k_cgS_dir(Dev g, const uint32_t* __restrict__ list, long long n,
+                          const double* __restrict__ invd, const double* __restrict__ rv,
                           double* __restrict__ pv, Ctl* ctl, const CgState* st) {
     count_launch(ctl);
     const double beta = st->first ? 0.0 : st->beta;
-    STREAM_LOOP(c, g.ncell) pv[c] = rv[c] * invd[c] + beta * pv[c];
+    WARP_STREAM_BEGIN(n)
+        uint32_t i[kU];
+        double r[kU], w[kU], p[kU];
+#pragma unroll
+        for (int j = 0; j < kU; ++j) i[j] = idx[j] < n ? list[idx[j]] : 0u;
+#pragma unroll
+        for (int j = 0; j < kU; ++j)
+            if (idx[j] < n) { r[j] = rv[i[j]]; w[j] = invd[i[j]]; p[j] = pv[i[j]]; }
+#pragma unroll
+        for (int j = 0; j < kU; ++j)
+            if (idx[j] < n) pv[i[j]] = r[j] * w[j] + beta * p[j];
+    WARP_STREAM_END
 }
 
-__device__ __forceinline__ double face_inv_diag(const Dev& g, uint8_t f) {
-    return 1.0 / (double)(2 * g.d + (f >> 1));
-}
-
-__global__ void k_cgS_matvec(Dev g, const uint8_t* __restrict__ mask,
+// q = S-hat p and p.q over the fluid-cell list: the sum over the open faces of
+// (p_c - p_nb) / (2d + g_f).
+__global__ void k_cgS_matvec(Dev g, const uint32_t* __restrict__ list, long long n,
                              const uint8_t* __restrict__ flags, const double* __restrict__ pv,
                              double* __restrict__ qv, Ctl* ctl, CgState* st, double* partials,
                              int slot) {
     count_launch(ctl);
     double v[1] = {0.0};
-    TILE_LOOP_BEGIN(g)
+    const long long plane = (long long)g.nx * g.ny;
+    const uint8_t* F0 = flags;
+    const uint8_t* F1 = flags + g.stride;
+    const uint8_t* F2 = flags + 2 * g.stride;
+    STREAM_LOOP(k, n) {
+        const uint32_t ci = list[k];
+        const FaceAt f = decode_face(g, ci);
+        const long long c = f.c;
+        const double pc = pv[c];
         double out = 0.0;
-        if (mask[c] == 1) {
-            const double pc = pv[c];
-            for (int a = 0; a < g.d; ++a) {
-                int ex, ey, ez;
-                axis_step(a, 1, ex, ey, ez);
-                const uint8_t fl = flags[(long long)a * g.stride + c];
-                if (fl & 1) out += (pc - pv[cell_at(g, x - ex, y - ey, z - ez)]) * face_inv_diag(g, fl);
-                const long long cu = cell_at(g, x + ex, y + ey, z + ez);
-                if (cu >= 0) {
-                    const uint8_t fu = flags[(long long)a * g.stride + cu];
-                    if (fu & 1) out += (pc - pv[cu]) * face_inv_diag(g, fu);
-                }
-            }
-            v[0] += pc * out;
+        // lower faces: an unknown lower face has its lower cell inside the box
+        uint8_t fl = F0[c];
+        if (fl & 1) out += (pc - pv[f.x > 0 ? c - 1 : c + g.nx - 1]) * tab5(g.wdiag, fl >> 1);
+        fl = F1[c];
+        if (fl & 1) out += (pc - pv[f.y > 0 ? c - g.nx : c + (long long)(g.ny - 1) * g.nx]) * tab5(g.wdiag, fl >> 1);
+        // upper faces
+        const long long xp = f.x < g.nx - 1 ? c + 1 : (g.per[0] ? c - (g.nx - 1) : -1);
+        if (xp >= 0) { fl = F0[xp]; if (fl & 1) out += (pc - pv[xp]) * tab5(g.wdiag, fl >> 1); }
+        const long long yp = f.y < g.ny - 1 ? c + g.nx : (g.per[1] ? c - (long long)(g.ny - 1) * g.nx : -1);
+        if (yp >= 0) { fl = F1[yp]; if (fl & 1) out += (pc - pv[yp]) * tab5(g.wdiag, fl >> 1); }
+        if (g.d == 3) {
+            fl = F2[c];
+            if (fl & 1) out += (pc - pv[f.z > 0 ? c - plane : c + (long long)(g.nz - 1) * plane]) * tab5(g.wdiag, fl >> 1);
+            const long long zp = f.z < g.nz - 1 ? c + plane : (g.per[2] ? c - (long long)(g.nz - 1) * plane : -1);
+            if (zp >= 0) { fl = F2[zp]; if (fl & 1) out += (pc - pv[zp]) * tab5(g.wdiag, fl >> 1); }
         }
         qv[c] = out;
-    TILE_LOOP_END
+        v[0] += pc * out;
+    }
     if (reduce_last_block<1>(v, partials, &ctl->ticket) && is_thread0()) {
         const double dq = v[0];
         if (!(dq > 0.0) || isinf(dq)) {
@@ -278,21 +425,39 @@ __global__ void k_cgS_matvec(Dev g, const uint8_t* __restrict__ mask,
     }
 }
 
-__global__ void k_cgS_update(Dev g, const double* __restrict__ invd, double* __restrict__ xv,
+__global__ void k_cgS_update(Dev g, const uint32_t* __restrict__ list, long long n,
+                             const double* __restrict__ invd, double* __restrict__ xv,
                              double* __restrict__ rv, const double* __restrict__ pv,
                              const double* __restrict__ qv, Ctl* ctl, CgState* st,
                              double* partials, int slot) {
     count_launch(ctl);
     const double alpha = st->alpha;
     double v[2] = {0.0, 0.0};
-    STREAM_LOOP(c, g.ncell) {
-        xv[c] += alpha * pv[c];
-        const double r = rv[c] - alpha * qv[c];
-        rv[c] = r;
-        const double zz = r * invd[c];
-        v[0] += r * zz;
-        v[1] += zz * zz;
-    }
+    WARP_STREAM_BEGIN(n)
+        uint32_t i[kU];
+        double xx[kU], p[kU], r[kU], q[kU], w[kU];
+#pragma unroll
+        for (int j = 0; j < kU; ++j) i[j] = idx[j] < n ? list[idx[j]] : 0u;
+#pragma unroll
+        for (int j = 0; j < kU; ++j)
+            if (idx[j] < n) {
+                xx[j] = xv[i[j]];
+                p[j] = pv[i[j]];
+                r[j] = rv[i[j]];
+                q[j] = qv[i[j]];
+                w[j] = invd[i[j]];
+            }
+#pragma unroll
+        for (int j = 0; j < kU; ++j)
+            if (idx[j] < n) {
+                xv[i[j]] = xx[j] + alpha * p[j];
+                const double rn = r[j] - alpha * q[j];
+                rv[i[j]] = rn;
+                const double zz = rn * w[j];
+                v[0] += rn * zz;
+                v[1] += zz * zz;
+            }
+    WARP_STREAM_END
     if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0())
         set_cond(ctl, slot, finish_inner(ctl, st, v[0], v[1]));
 }
@@ -602,16 +767,32 @@ static inline dim3 sgrid(const Handle& H, long long n) {
     return dim3((unsigned)(nb < H.target_blocks ? (nb > 0 ? nb : 1) : H.target_blocks));
 }
 static inline dim3 sblock() { return dim3(kBlock); }
+// column-tile grid: x = strided x-y tiles, y = z chunks, z = fields
+static inline dim3 cgrid(const Handle& H, int fields) {
+    const long long tiles = (long long)((H.g.nx + kTileX - 1) / kTileX) * ((H.g.ny + kTileY - 1) / kTileY);
+    const long long target = H.target_blocks;
+    long long zs = 1, gxx = tiles;
+    if (tiles * fields >= target) {
+        gxx = (target + fields - 1) / fields;
+    } else {
+        zs = (target + tiles * fields - 1) / (tiles * fields);
+        if (zs > H.g.nz) zs = H.g.nz;
+    }
+    if (gxx < 1) gxx = 1;
+    return dim3((unsigned)gxx, (unsigned)zs, (unsigned)fields);
+}
 
 // One inner A solve with the right-hand side already formed by k_cgA_init (slot s).
 static void record_A_loop(Handle& H, Recorder& R, CgState* st, int s) {
-    const long long nf = (long long)H.g.d * H.g.stride;
-    R.loop(s, [&, st, s, nf](Recorder& B) {
-        B.launch("cgA_dir", k_cgA_dir, sgrid(H, nf), sblock(), H.g, H.flags, H.ar, H.ap, H.dctl, st);
-        B.launch("cgA_matvec", k_cgA_matvec, tgrid(H), tblock(), H.g, H.flags, H.ap, H.aq, H.dctl,
-                 st, H.partials, s);
-        B.launch("cgA_update", k_cgA_update, sgrid(H, nf), sblock(), H.g, H.flags, H.ax, H.ar, H.ap,
-                 H.aq, H.dctl, st, H.partials, s);
+    const long long nu = H.n_u;
+    R.loop(s, [&, st, s, nu](Recorder& B) {
+        B.launch("cgA_dir", k_cgA_dir, sgrid(H, nu), sblock(), H.g, (const uint32_t*)H.ulist, nu,
+                 (const uint8_t*)H.flags, (const double*)H.ar, H.ap, H.dctl, (const CgState*)st);
+        B.launch("cgA_matvec", k_cgA_matvec, sgrid(H, nu), sblock(), H.g, (const uint32_t*)H.ulist,
+                 nu, (const uint8_t*)H.flags, (const double*)H.ap, H.aq, H.dctl, st, H.partials, s);
+        B.launch("cgA_update", k_cgA_update, sgrid(H, nu), sblock(), H.g, (const uint32_t*)H.ulist,
+                 nu, (const uint8_t*)H.flags, H.ax, H.ar, (const double*)H.ap, (const double*)H.aq,
+                 H.dctl, st, H.partials, s);
     });
 }
 
@@ -639,12 +820,13 @@ static void record_S_solve(Handle& H, Recorder& R, int s) {
              (const int*)H.cmp, (const double*)H.cmean, H.orr, H.sx, H.sr, H.dctl, st,
              (const CgState*)&H.dctl->out, H.partials, s);
     R.loop(s, [&, st, s](Recorder& B) {
-        B.launch("cgS_dir", k_cgS_dir, sgrid(H, H.g.ncell), sblock(), H.g, (const double*)H.invdS,
-                 (const double*)H.sr, H.sp, H.dctl, (const CgState*)st);
-        B.launch("cgS_matvec", k_cgS_matvec, tgrid(H), tblock(), H.g, H.mask, H.flags,
-                 (const double*)H.sp, H.sq, H.dctl, st, H.partials, s);
-        B.launch("cgS_update", k_cgS_update, sgrid(H, H.g.ncell), sblock(), H.g,
-                 (const double*)H.invdS, H.sx, H.sr, (const double*)H.sp, (const double*)H.sq,
+        const long long np = H.n_p;
+        B.launch("cgS_dir", k_cgS_dir, sgrid(H, np), sblock(), H.g, (const uint32_t*)H.flist, np,
+                 (const double*)H.invdS, (const double*)H.sr, H.sp, H.dctl, (const CgState*)st);
+        B.launch("cgS_matvec", k_cgS_matvec, sgrid(H, np), sblock(), H.g, (const uint32_t*)H.flist,
+                 np, (const uint8_t*)H.flags, (const double*)H.sp, H.sq, H.dctl, st, H.partials, s);
+        B.launch("cgS_update", k_cgS_update, sgrid(H, np), sblock(), H.g, (const uint32_t*)H.flist,
+                 np, (const double*)H.invdS, H.sx, H.sr, (const double*)H.sp, (const double*)H.sq,
                  H.dctl, st, H.partials, s);
     });
 }
@@ -658,7 +840,7 @@ void record_solve(Handle& H, Recorder& R, int precond) {
     const int s_s0 = R.new_slot();
     const int s_a = R.new_slot();
     const int s_s = R.new_slot();
-    R.launch("cgA_init", k_cgA_init, tgrid(H), tblock(), H.g, H.flags, H.ax, H.ar,
+    R.launch("cgA_init", k_cgA_init, cgrid(H, H.g.d), tblock(), H.g, H.flags, H.ax, H.ar,
              (const double*)nullptr, 0.0, 1.0, (const double*)nullptr, ctl, inA, H.partials, s_rhs);
     record_A_loop(H, R, inA, s_rhs);
     R.launch("outer_init", k_outer_init, tgrid(H), tblock(), H.g, H.mask, H.flags,
@@ -671,7 +853,7 @@ void record_solve(Handle& H, Recorder& R, int precond) {
     }
     R.loop(s_out, [&, ctl, inA, precond, s_out, s_a, s_s](Recorder& B) {
         // q = S d = B A^-1 B^T d
-        B.launch("cgA_init", k_cgA_init, tgrid(H), tblock(), H.g, H.flags, H.ax, H.ar,
+        B.launch("cgA_init", k_cgA_init, cgrid(H, H.g.d), tblock(), H.g, H.flags, H.ax, H.ar,
                  (const double*)H.od, 1.0, 0.0, (const double*)nullptr, ctl, inA, H.partials, s_a);
         record_A_loop(H, B, inA, s_a);
         B.launch("outer_div", k_outer_div, tgrid(H), tblock(), H.g, H.mask, H.flags,
@@ -693,7 +875,7 @@ void record_recover(Handle& H, Recorder& R) {
     Ctl* ctl = H.dctl;
     CgState* inA = &ctl->inA;
     const int s = R.new_slot();
-    R.launch("cgA_init", k_cgA_init, tgrid(H), tblock(), H.g, H.flags, H.ax, H.ar,
+    R.launch("cgA_init", k_cgA_init, cgrid(H, H.g.d), tblock(), H.g, H.flags, H.ax, H.ar,
              (const double*)H.op, -1.0, 1.0, (const double*)nullptr, ctl, inA, H.partials, s);
     record_A_loop(H, R, inA, s);
     const long long nf = (long long)H.g.d * H.g.stride;
@@ -705,7 +887,7 @@ void record_solve_A(Handle& H, Recorder& R, const double* b, double* x) {
     Ctl* ctl = H.dctl;
     CgState* st = &ctl->solo;
     const int s = R.new_slot();
-    R.launch("cgA_init", k_cgA_init, tgrid(H), tblock(), H.g, H.flags, H.ax, H.ar,
+    R.launch("cgA_init", k_cgA_init, cgrid(H, H.g.d), tblock(), H.g, H.flags, H.ax, H.ar,
              (const double*)nullptr, 0.0, 0.0, b, ctl, st, H.partials, s);
     record_A_loop(H, R, st, s);
     (void)x;
@@ -721,32 +903,35 @@ cudaError_t time_kernel(Handle& H, int which, int slot, float* ms) {
     }
     Ctl* ctl = H.dctl;
     CgState* st = &ctl->solo;
-    const long long nf = (long long)H.g.d * H.g.stride;
     cudaError_t e = cudaEventRecord(H.ev0, H.stream);
     if (e != cudaSuccess) return e;
+    const long long nu = H.n_u, np = H.n_p;
     switch (which) {
         case 0:
-            k_cgA_dir<<<sgrid(H, nf), sblock(), 0, H.stream>>>(H.g, H.flags, H.ar, H.ap, ctl, st);
+            k_cgA_dir<<<sgrid(H, nu), sblock(), 0, H.stream>>>(H.g, H.ulist, nu, H.flags, H.ar, H.ap,
+                                                               ctl, st);
             break;
         case 1:
-            k_cgA_matvec<<<tgrid(H), tblock(), 0, H.stream>>>(H.g, H.flags, H.ap, H.aq, ctl, st,
-                                                              H.partials, slot);
-            break;
-        case 2:
-            k_cgA_update<<<sgrid(H, nf), sblock(), 0, H.stream>>>(H.g, H.flags, H.ax, H.ar, H.ap,
+            k_cgA_matvec<<<sgrid(H, nu), sblock(), 0, H.stream>>>(H.g, H.ulist, nu, H.flags, H.ap,
                                                                   H.aq, ctl, st, H.partials, slot);
             break;
+        case 2:
+            k_cgA_update<<<sgrid(H, nu), sblock(), 0, H.stream>>>(H.g, H.ulist, nu, H.flags, H.ax,
+                                                                  H.ar, H.ap, H.aq, ctl, st,
+                                                                  H.partials, slot);
+            break;
         case 3:
-            k_cgS_dir<<<sgrid(H, H.g.ncell), sblock(), 0, H.stream>>>(H.g, H.invdS, H.sr, H.sp,
-                                                                      ctl, st);
+            k_cgS_dir<<<sgrid(H, np), sblock(), 0, H.stream>>>(H.g, H.flist, np, H.invdS, H.sr,
+                                                               H.sp, ctl, st);
             break;
         case 4:
-            k_cgS_matvec<<<tgrid(H), tblock(), 0, H.stream>>>(H.g, H.mask, H.flags, H.sp, H.sq,
-                                                              ctl, st, H.partials, slot);
+            k_cgS_matvec<<<sgrid(H, np), sblock(), 0, H.stream>>>(H.g, H.flist, np, H.flags, H.sp,
+                                                                  H.sq, ctl, st, H.partials, slot);
             break;
         case 5:
-            k_cgS_update<<<sgrid(H, H.g.ncell), sblock(), 0, H.stream>>>(
-                H.g, H.invdS, H.sx, H.sr, H.sp, H.sq, ctl, st, H.partials, slot);
+            k_cgS_update<<<sgrid(H, np), sblock(), 0, H.stream>>>(H.g, H.flist, np, H.invdS, H.sx,
+                                                                  H.sr, H.sp, H.sq, ctl, st,
+                                                                  H.partials, slot);
             break;
         default:
             return cudaErrorInvalidValue;

@@ -151,8 +151,10 @@ def test_full_solve_matches_oracle(cuda, name, force, tol, iters_comparable, pre
     g.recover_velocity()
     p = cell_device_to_compact(geo, g.field(binding.FIELD_P))
     u = face_device_to_compact(g, geo, g.field(binding.FIELD_U))
-    # velocity: relative L2 within 1e-9 (h^2 sqrt(n_u) is the scale of a one-voxel flow)
-    scale_u = max(np.linalg.norm(ref["u"]), geo.h ** 2 * np.sqrt(geo.n_u))
+    # velocity: relative L2 within 1e-9 of the flow scale max(||u||, ||A^-1 f||); the
+    # second term matters where the force is balanced by pressure and u is ~0
+    u_f = prob.solve_A(mac.force(geo, force), 1e-12, 20000).x
+    scale_u = max(np.linalg.norm(ref["u"]), np.linalg.norm(u_f))
     assert np.linalg.norm(u - ref["u"]) <= 1e-9 * scale_u
     # pressure (defined up to constants per component): both iterates meet
     # ||S p - g|| <= tol ||g||, so ||S (p - p_ref)|| <= 2 tol ||g|| plus the inner-solve slack
