@@ -167,6 +167,23 @@ int schur_solve_A(schur_geom_t g, const double* b, double* x, double tol, int ma
  * contents after the last call); results of later calls are unaffected.  Synchronises. */
 int schur_time_kernel(schur_geom_t g, int kernel, float* ms);
 
+/* Allocation-free Darcy permeability of a caller-owned velocity field (no counterpart in
+ * the paper: an entry point for callers that may not allocate device memory, e.g. code
+ * running inside a memory pool it does not own or inside an already-captured graph).
+ * u and flags are device buffers in the face layout [ndim][face_stride] (FP64 velocity,
+ * flag bytes with bit 0 = unknown); dims are n_x, n_y, n_z as for
+ * schur_create_geometry.  k_dev is a device array of 3 doubles that receives, for each
+ * axis a < ndim, the sum of u_a over the unknown faces divided by the cell count (0 for
+ * the other entries).  Runs on `stream` (a cudaStream_t) without synchronising.
+ * It calls no cudaMalloc or cudaFree: its scratch is a static device array of 96 KiB
+ * held by every device that loads the library until exit, so ndim * face_stride may not
+ * exceed 8388608 faces (SCHUR_EINVAL otherwise).  The first call on a device looks up
+ * the array's device address; make that first call before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU race and must be serialised. */
+int schur_permeability_noalloc(const double* u, const uint8_t* flags, int ndim,
+                               const int64_t dims[3], int64_t face_stride, void* stream,
+                               double* k_dev);
+
 /* Release the handle and all its device memory (NULL is ignored). */
 void schur_destroy(schur_geom_t g);
 

@@ -28,7 +28,7 @@ EXPORTED = [
     "schur_recover_velocity", "schur_permeability", "schur_get_field",
     "schur_geometry_info", "schur_apply_A", "schur_apply_B", "schur_apply_BT",
     "schur_apply_simple", "schur_solve_A", "schur_time_kernel", "schur_destroy",
-    "schur_last_error",
+    "schur_last_error", "schur_permeability_noalloc",
 ]
 KERNELS = {"cgA_dir": 0, "cgA_matvec": 1, "cgA_update": 2, "cgS_dir": 3, "cgS_matvec": 4,
            "cgS_update": 5}
@@ -89,6 +89,7 @@ def load(build_if_missing: bool = True):
         "schur_apply_simple": (C.c_int, [vp, vp, vp]),
         "schur_solve_A": (C.c_int, [vp, vp, vp, C.c_double, C.c_int, C.POINTER(C.c_int)]),
         "schur_time_kernel": (C.c_int, [vp, C.c_int, C.POINTER(C.c_float)]),
+        "schur_permeability_noalloc": (C.c_int, [vp, vp, C.c_int, i64p, C.c_int64, vp, vp]),
         "schur_destroy": (None, [vp]),
         "schur_last_error": (C.c_char_p, []),
     }
@@ -254,6 +255,16 @@ class Geometry:
         ms = C.c_float()
         _check(load().schur_time_kernel(self._h, KERNELS[name], C.byref(ms)))
         return ms.value
+
+    def permeability_noalloc(self, k_out, u=None, flags=None):
+        """Darcy permeability of a face velocity field through the allocation-free entry
+        point; k_out is a CUDA float64 tensor of 3 entries (written asynchronously)."""
+        u = self.field(FIELD_U) if u is None else u
+        flags = self.field(FIELD_FLAGS) if flags is None else flags
+        dims = (C.c_int64 * 3)(*(list(reversed(self.shape)) + [1] * (3 - self.ndim)))
+        _check(load().schur_permeability_noalloc(_ptr(u), _ptr(flags), self.ndim, dims,
+                                                 self.face_stride, C.c_void_p(self.stream),
+                                                 _ptr(k_out)))
 
     # ---- layout helpers ----
     @property

@@ -247,6 +247,8 @@ int map_status(int st) {
 
 }  // namespace
 
+int schur_set_error_internal(int code, const char* msg) { return set_error(code, msg); }
+
 extern "C" {
 
 void schur_opts_default(schur_opts* o) {

@@ -76,3 +76,6 @@ void record_solve_A(Handle& H, Recorder& R, const double* b, double* x);
 cudaError_t time_kernel(Handle& H, int which, int slot, float* ms);
 
 }  // namespace schur
+
+// api.cu: record an error for schur_last_error() and return `code`
+int schur_set_error_internal(int code, const char* msg);
