@@ -1,0 +1,56 @@
+"""Full-size parity: the CUDA path against oracle runs stored by oracle/record_reference.py
+(64^3 and 128^3 periodic sphere packings, radii U[4,8), porosity 0.40, f = e_x, tol 1e-8,
+inner 1e-12).  Permeability within 1e-8 relative, outer and inner iteration counts
+within 2, plus properties of the GPU solution checked with the oracle's own operators
+(divergence-free velocity, momentum residual)."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import mac, stokes
+from paper_2307_05266_gb300 import binding, synth
+
+from gpu_helpers import cell_device_to_compact, face_device_to_compact
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+PRECONDS = {"uzawa": binding.UZAWA, "simple": binding.SIMPLE}
+
+
+def _golden(workload, pc):
+    with open(os.path.join(GOLDEN, f"oracle_{workload}_{pc}.json")) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("workload,n", [("spheres64", 64), ("spheres128", 128)])
+@pytest.mark.parametrize("pc", ["uzawa", "simple"])
+def test_fullsize_against_recorded_oracle(workload, n, pc):
+    ref = _golden(workload, pc)
+    torch.cuda.set_device(0)
+    mask = synth.sphere_packing(n, 4.0, 8.0, 0.40, 0)
+    with binding.Geometry(mask) as g:
+        info = g.geometry_info()
+        assert sum(info.n_unknown[a] for a in range(3)) == ref["n_unknown"]
+        assert info.n_fluid == ref["n_fluid"]
+        g.set_force((1.0, 0.0, 0.0))
+        st = g.solve(precond=PRECONDS[pc], tol=1e-8)
+        rec = g.recover_velocity()
+        k = [g.permeability(a) for a in range(3)]
+        assert abs(st.outer_iters - ref["outer_iters"]) <= 2
+        assert abs(st.inner_iters_A - ref["inner_iters_A"]) <= 2 * max(1, ref["outer_iters"])
+        assert abs(rec.inner_iters_A - ref["recovery_iters"]) <= 2
+        assert abs(k[0] - ref["k"][0]) <= 1e-8 * abs(ref["k"][0])
+        if n == 64:
+            # properties of the GPU solution with the oracle's assembled operators
+            prob = stokes.StokesProblem(mask)
+            geo = prob.geo
+            u = face_device_to_compact(g, geo, g.field(binding.FIELD_U))
+            p = cell_device_to_compact(geo, g.field(binding.FIELD_P))
+            div = prob.B @ u
+            assert np.linalg.norm(div) <= 1e-7 * np.linalg.norm(abs(prob.B) @ np.abs(u))
+            res = prob.A @ u - (mac.force(geo, (1.0, 0.0, 0.0)) - prob.BT @ p)
+            assert np.linalg.norm(res) <= 1e-9 * np.linalg.norm(prob.A @ u)
