@@ -334,3 +334,65 @@ def test_planted_alg1_printed_sign():
         d = r_new + beta * d
         r = z = r_new
     assert np.linalg.norm(S @ p - g) > 1e-3 * np.linalg.norm(g)
+
+
+# ---- nullspace handling of the SIMPLE solve (Section 3.2, "special care") ------
+def _bfs_components(mask, periodic):
+    """Brute force: flood fill over fluid cells through faces whose two cells are fluid."""
+    d = mask.ndim
+    shape = mask.shape
+    lab = -np.ones(shape, dtype=np.int64)
+    n = 0
+    for start in zip(*np.nonzero(mask)):
+        if lab[start] >= 0:
+            continue
+        stack = [start]
+        lab[start] = n
+        while stack:
+            c = stack.pop()
+            for ax in range(d):
+                for s in (-1, 1):
+                    nb = list(c)
+                    nb[ax] += s
+                    a = d - 1 - ax
+                    if not (0 <= nb[ax] < shape[ax]):
+                        if not periodic[a]:
+                            continue
+                        nb[ax] %= shape[ax]
+                    nb = tuple(nb)
+                    if mask[nb] and lab[nb] < 0:
+                        lab[nb] = n
+                        stack.append(nb)
+        n += 1
+    return n, lab
+
+
+@pytest.mark.parametrize("shape,phi,seed,periodic", SMALL_GEOMETRIES)
+def test_fluid_components_match_flood_fill(shape, phi, seed, periodic):
+    mask = _random_mask(shape, phi, seed)
+    per = periodic or (True,) * len(shape)
+    geo = mac.classify(mask, per)
+    n, comp = stokes.fluid_components(geo)
+    n_ref, lab = _bfs_components(mask, per)
+    assert n == n_ref
+    # same partition: labels agree up to renaming
+    ref = lab[mask.astype(bool)]
+    pairs = set(zip(comp.tolist(), ref.tolist()))
+    assert len(pairs) == n
+
+
+def test_simple_solve_projects_onto_range():
+    """z = S-hat^+ r: with r carrying a constant per component (rounding in the outer
+    residual), the projected solve still converges, S-hat z equals the projected r and z
+    has zero mean on every component."""
+    mask = synth.sphere_packing(16, 2.0, 4.0, 0.3, seed=1)
+    prob = stokes.StokesProblem(mask)
+    assert prob.n_comp > 1
+    rng = np.random.default_rng(0)
+    r = prob.remove_mean(rng.standard_normal(prob.geo.n_p))
+    r_noisy = r + 1e-3 * np.ones_like(r)
+    res = prob.solve_simple(r_noisy, 1e-12, 20000)
+    assert res.status == krylov.OK
+    np.testing.assert_allclose(prob.S_simple @ res.x, r, atol=1e-9 * np.abs(r).max())
+    means = np.bincount(prob.comp, weights=res.x) / prob.comp_size
+    assert np.abs(means).max() < 1e-12 * max(1.0, np.abs(res.x).max())
