@@ -64,12 +64,16 @@ typedef struct schur_geom* schur_geom_t;
 
 /* Solver options.  Defaults (schur_opts_default): SIMPLE, unpreconditioned stop,
  * FP64, graph loop, tol 1e-8, tol_inner_A = tol_inner_S = 1e-12, max_outer 2000,
- * max_inner 20000. */
+ * max_inner 20000; mixed precision: tol_inner_f32 1e-5, refine_factor 1e-3,
+ * max_refine 30, step_max 1000. */
 typedef struct {
     int precond;        /* SCHUR_UZAWA | SCHUR_SIMPLE (eq. schur_uzawa_prec)                */
     int stop_norm;      /* SCHUR_STOP_UNPRECOND: ||r_k||/||r_0|| < tol (Section 4.2.2);
                            SCHUR_STOP_PRECOND: ||z_k||/||z_0|| < tol (Algorithm 1)          */
-    int precision;      /* SCHUR_FP64 (SCHUR_MIXED is reserved: returns SCHUR_EINVAL)      */
+    int precision;      /* SCHUR_FP64: everything in FP64 (Algorithm 1 as in the paper);
+                           SCHUR_MIXED: FP32 inner A and SIMPLE solves inside an FP64
+                           flexible outer CG (Notay FCG(1)) wrapped in FP64 defect
+                           correction; the stop is on the FP64 true residual            */
     int loop_mode;      /* SCHUR_LOOP_GRAPH: one CUDA graph with device-side while loops;
                            SCHUR_LOOP_HOST: the host drives every loop (debugging)         */
     int max_outer;      /* cap on outer iterations (S applications)                         */
@@ -77,6 +81,10 @@ typedef struct {
     double tol;         /* outer relative tolerance eps_S                                   */
     double tol_inner_A; /* inner tolerance eps_A: ||M^-1 r||/||M^-1 r_0|| (Section 3.2)     */
     double tol_inner_S; /* inner tolerance eps_S-hat for the SIMPLE solve (Section 3.2)     */
+    double tol_inner_f32;  /* MIXED: tolerance of the FP32 inner solves (default 1e-5)      */
+    double refine_factor;  /* MIXED: residual reduction of one refinement step (1e-3)       */
+    int max_refine;        /* MIXED: cap on refinement steps (true residuals) (30)          */
+    int step_max;          /* MIXED: cap on FCG iterations in one step (1000)               */
 } schur_opts;
 
 typedef struct {
@@ -90,6 +98,9 @@ typedef struct {
     double rel_res_precond;      /* ||z_k|| / ||z_0|| at exit (NaN when not formed)        */
     double g_norm;               /* ||g||_2                                                */
     long long kernel_launches;   /* kernels this call ran on the GPU                       */
+    long long inner_iters_A_f32; /* MIXED: FP32 inner A iterations (inner_iters_A: FP64)   */
+    long long inner_iters_S_f32; /* MIXED: FP32 inner SIMPLE iterations                    */
+    int refinements;             /* MIXED: refinement steps (FP64 true residuals formed)   */
 } schur_stats;
 
 typedef struct {
@@ -163,7 +174,7 @@ int schur_solve_A(schur_geom_t g, const double* b, double* x, double tol, int ma
 /* Profiling hook: one launch of a hot solver kernel on the handle's stream, bracketed by
  * two CUDA events; *ms receives the elapsed time.  kernel: 0 inner-A direction update,
  * 1 inner-A stencil A p (with p.q), 2 inner-A x/r update (with r.z, z.z), 3-5 the same
- * three for the SIMPLE operator.  The kernel works on the solver's own buffers (their
+ * three for the SIMPLE operator, 6-11 the FP32 versions of 0-5 (after a mixed solve).  The kernel works on the solver's own buffers (their
  * contents after the last call); results of later calls are unaffected.  Synchronises. */
 int schur_time_kernel(schur_geom_t g, int kernel, float* ms);
 

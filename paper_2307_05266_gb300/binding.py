@@ -31,13 +31,16 @@ EXPORTED = [
     "schur_last_error", "schur_permeability_noalloc",
 ]
 KERNELS = {"cgA_dir": 0, "cgA_matvec": 1, "cgA_update": 2, "cgS_dir": 3, "cgS_matvec": 4,
-           "cgS_update": 5}
+           "cgS_update": 5, "cgA_dir_f32": 6, "cgA_matvec_f32": 7, "cgA_update_f32": 8,
+           "cgS_dir_f32": 9, "cgS_matvec_f32": 10, "cgS_update_f32": 11}
 
 
 class Opts(C.Structure):
     _fields_ = [("precond", C.c_int), ("stop_norm", C.c_int), ("precision", C.c_int),
                 ("loop_mode", C.c_int), ("max_outer", C.c_int), ("max_inner", C.c_int),
-                ("tol", C.c_double), ("tol_inner_A", C.c_double), ("tol_inner_S", C.c_double)]
+                ("tol", C.c_double), ("tol_inner_A", C.c_double), ("tol_inner_S", C.c_double),
+                ("tol_inner_f32", C.c_double), ("refine_factor", C.c_double),
+                ("max_refine", C.c_int), ("step_max", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -45,7 +48,8 @@ class Stats(C.Structure):
                 ("inner_status", C.c_int), ("inner_iters_A", C.c_longlong),
                 ("inner_iters_S", C.c_longlong), ("rel_res", C.c_double),
                 ("rel_res_precond", C.c_double), ("g_norm", C.c_double),
-                ("kernel_launches", C.c_longlong)]
+                ("kernel_launches", C.c_longlong), ("inner_iters_A_f32", C.c_longlong),
+                ("inner_iters_S_f32", C.c_longlong), ("refinements", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

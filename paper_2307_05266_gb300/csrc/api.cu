@@ -48,7 +48,7 @@ cudaError_t alloc(Handle& H, T** p, size_t n) {
 }
 
 void free_all(Handle& H) {
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 4; ++k) {
         if (H.exec_solve[k]) cudaGraphExecDestroy(H.exec_solve[k]);
         if (H.graph_solve[k]) cudaGraphDestroy(H.graph_solve[k]);
         H.exec_solve[k] = nullptr;
@@ -62,7 +62,8 @@ void free_all(Handle& H) {
     H.graph_recover = H.graph_solo = nullptr;
     void* bufs[] = {H.mask, H.flags, H.invdS, H.ax, H.ar, H.ap, H.aq, H.sx, H.sr, H.sp,
                     H.sq, H.op, H.orr, H.od, H.oq, H.og, H.u, H.partials, H.dctl,
-                    H.cmp, H.cmean, H.small_start, H.small_cells, H.ulist, H.flist};
+                    H.cmp, H.cmean, H.small_start, H.small_cells, H.ulist, H.flist,
+                    H.axf, H.arf, H.apf, H.aqf, H.sxf, H.srf, H.spf, H.sqf, H.invdSf};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (H.hctl) cudaFreeHost(H.hctl);
@@ -262,6 +263,10 @@ void schur_opts_default(schur_opts* o) {
     o->tol = 1e-8;
     o->tol_inner_A = 1e-12;
     o->tol_inner_S = 1e-12;
+    o->tol_inner_f32 = 1e-5;
+    o->refine_factor = 1e-3;
+    o->max_refine = 30;
+    o->step_max = 1000;
 }
 
 const char* schur_last_error(void) { return g_last_error.c_str(); }
@@ -300,6 +305,8 @@ int schur_create_geometry(const uint8_t* mask, int ndim, const int64_t dims[3],
     for (int k = 0; k < 5; ++k) {
         g.diag[k] = (double)(2 * ndim + k);
         g.wdiag[k] = 1.0 / g.diag[k];
+        g.diagf[k] = (float)g.diag[k];
+        g.wdiagf[k] = (float)g.wdiag[k];
     }
 
     int dev = 0;
@@ -405,13 +412,30 @@ int schur_solve(schur_geom_t G, const schur_opts* opts, schur_stats* stats) {
         return set_error(SCHUR_EINVAL, "precond must be SCHUR_UZAWA or SCHUR_SIMPLE");
     if (o.stop_norm != SCHUR_STOP_UNPRECOND && o.stop_norm != SCHUR_STOP_PRECOND)
         return set_error(SCHUR_EINVAL, "bad stop_norm");
-    if (o.precision != SCHUR_FP64) return set_error(SCHUR_EINVAL, "only SCHUR_FP64 is available");
+    if (o.precision != SCHUR_FP64 && o.precision != SCHUR_MIXED)
+        return set_error(SCHUR_EINVAL, "precision must be SCHUR_FP64 or SCHUR_MIXED");
+    if (o.precision == SCHUR_MIXED &&
+        (!(o.tol_inner_f32 > 0) || !(o.refine_factor > 0 && o.refine_factor < 1) ||
+         o.max_refine < 1 || o.step_max < 1))
+        return set_error(SCHUR_EINVAL, "mixed precision needs tol_inner_f32 > 0, "
+                                       "0 < refine_factor < 1, max_refine >= 1, step_max >= 1");
     if (o.loop_mode != SCHUR_LOOP_GRAPH && o.loop_mode != SCHUR_LOOP_HOST)
         return set_error(SCHUR_EINVAL, "bad loop_mode");
     if (!(o.tol > 0) || !(o.tol_inner_A > 0) || !(o.tol_inner_S > 0) || o.max_outer < 1 ||
         o.max_inner < 1)
         return set_error(SCHUR_EINVAL, "tolerances must be > 0 and caps >= 1");
     Handle& H = G->H;
+    if (o.precision == SCHUR_MIXED && !H.axf) {
+        // FP32 inner-solve buffers, allocated on the first mixed-precision solve
+        const size_t nf = (size_t)H.g.d * H.g.stride, nc = (size_t)H.g.ncell;
+        cudaError_t e = cudaSuccess;
+        auto A = [&](float** p, size_t n) { if (e == cudaSuccess) e = alloc(H, p, n); };
+        A(&H.axf, nf); A(&H.arf, nf); A(&H.apf, nf); A(&H.aqf, nf);
+        A(&H.sxf, nc); A(&H.srf, nc); A(&H.spf, nc); A(&H.sqf, nc); A(&H.invdSf, nc);
+        if (e == cudaSuccess) e = launch_to_float(H, H.invdS, H.invdSf, (long long)nc);
+        if (e == cudaErrorMemoryAllocation) return set_error(SCHUR_ENOMEM, "device allocation failed");
+        if (e != cudaSuccess) return cuda_error(e, "mixed-precision buffers");
+    }
     Ctl* c = H.hctl;
     reset_call(H, o.loop_mode == SCHUR_LOOP_GRAPH);
     c->precond = o.precond;
@@ -422,19 +446,30 @@ int schur_solve(schur_geom_t G, const schur_opts* opts, schur_stats* stats) {
     c->inS.max_iter = o.max_inner;
     c->out.tol = o.tol;
     c->out.max_iter = o.max_outer;
+    c->inA32.tol = o.tol_inner_f32;
+    c->inA32.max_iter = o.max_inner;
+    c->inS32.tol = o.tol_inner_f32;
+    c->inS32.max_iter = o.max_inner;
+    c->inA32.total = c->inS32.total = 0;
+    c->mix.max_refine = o.max_refine;
+    c->mix.step_max = o.step_max;
+    c->mix.factor = o.refine_factor;
+    c->mix.refine = 0;
+    c->mix.stop = 0;
     c->zero_rhs = 0;
     int rc;
+    const int gi = o.precision * 2 + o.precond;
     if (o.loop_mode == SCHUR_LOOP_GRAPH) {
-        rc = build_graph(H, &H.graph_solve[o.precond], &H.exec_solve[o.precond],
-                         [&](Recorder& R) { record_solve(H, R, o.precond); });
+        rc = build_graph(H, &H.graph_solve[gi], &H.exec_solve[gi],
+                         [&](Recorder& R) { record_solve(H, R, o.precond, o.precision); });
         if (rc) return rc;
         if ((rc = upload(H))) return rc;
-        CUDA_TRY(cudaGraphLaunch(H.exec_solve[o.precond], H.stream), "cudaGraphLaunch");
+        CUDA_TRY(cudaGraphLaunch(H.exec_solve[gi], H.stream), "cudaGraphLaunch");
     } else {
         if ((rc = upload(H))) return rc;
         int slot = kHostSlotBase;
         Recorder R(H.stream, H.dctl, &slot);
-        record_solve(H, R, o.precond);
+        record_solve(H, R, o.precond, o.precision);
         if (!R.ok()) return cuda_error(R.error(), R.where().c_str());
     }
     if ((rc = download(H))) return rc;
@@ -443,6 +478,7 @@ int schur_solve(schur_geom_t G, const schur_opts* opts, schur_stats* stats) {
     H.last_tolA = o.tol_inner_A;
     H.last_max_inner = o.max_inner;
     H.last_loop = o.loop_mode;
+    H.last_precision = o.precision;
     if (stats) {
         stats->status = map_status(c->out.status);
         stats->outer_iters = c->out.iter;
@@ -454,6 +490,9 @@ int schur_solve(schur_geom_t G, const schur_opts* opts, schur_stats* stats) {
         stats->rel_res_precond = c->out.relz;
         stats->g_norm = std::sqrt(c->g_norm2);
         stats->kernel_launches = c->launches;
+        stats->inner_iters_A_f32 = c->inA32.total;
+        stats->inner_iters_S_f32 = c->inS32.total;
+        stats->refinements = o.precision == SCHUR_MIXED ? c->mix.refine : 0;
     }
     const int st = map_status(c->out.status);
     if (st != SCHUR_OK) set_error(st, "outer iteration did not converge");
@@ -600,7 +639,9 @@ int schur_solve_A(schur_geom_t G, const double* b, double* x, double tol, int ma
 
 int schur_time_kernel(schur_geom_t G, int kernel, float* ms) {
     if (!G || !ms) return set_error(SCHUR_EINVAL, "null argument");
-    if (kernel < 0 || kernel > 5) return set_error(SCHUR_EINVAL, "kernel id must be 0..5");
+    if (kernel < 0 || kernel > 11) return set_error(SCHUR_EINVAL, "kernel id must be 0..11");
+    if (kernel > 5 && !G->H.axf)
+        return set_error(SCHUR_ESTATE, "FP32 kernels need a mixed-precision solve first");
     Handle& H = G->H;
     reset_call(H, 0);  // no graph: the condition slot is only written to device memory
     int rc = upload(H);

@@ -40,7 +40,18 @@ struct Dev {
     // throughput, so no FP64 division or conversion appears in the hot loops)
     double diag[5];   // 2d + g: diagonal of the dimensionless operator h^2 A
     double wdiag[5];  // 1 / (2d + g)
+    float diagf[5];   // the same in FP32
+    float wdiagf[5];
 };
+
+__device__ __forceinline__ float tab5f(const float (&t)[5], int k) {
+    float v = t[0];
+    v = (k == 1) ? t[1] : v;
+    v = (k == 2) ? t[2] : v;
+    v = (k == 3) ? t[3] : v;
+    v = (k == 4) ? t[4] : v;
+    return v;
+}
 
 __device__ __forceinline__ double tab5(const double (&t)[5], int k) {
     double v = t[0];
@@ -70,6 +81,19 @@ struct CgState {
     long long total;  // iterations summed over every solve of this kind in the call
 };
 
+// Defect-correction state of the mixed-precision solve.
+struct Mix {
+    int refine;       // refinement steps done (true residuals formed)
+    int max_refine;
+    int step_iter;    // FCG iterations in the current step
+    int step_max;
+    int stop;         // breakdown: leave every loop
+    int pad;
+    double rr_step0;  // ||r||^2 at the start of the step
+    double factor;    // the step ends when ||r|| <= factor * ||r_step0||
+    double dq;        // d.q of the last FCG direction
+};
+
 struct Ctl {
     // options (host-written before a launch)
     int precond, stop_norm, use_graph, pad0;
@@ -78,7 +102,8 @@ struct Ctl {
     unsigned long long handle[kSlots];
     unsigned int cond[kSlots];
     // Krylov instances
-    CgState inA, inS, out, solo;
+    CgState inA, inS, out, solo, inA32, inS32;
+    Mix mix;
     // results
     double g_norm2, g_scale2;
     int zero_rhs, inner_status;

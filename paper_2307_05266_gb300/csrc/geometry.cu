@@ -197,6 +197,17 @@ __global__ void k_apply_simple(Dev g, const uint8_t* __restrict__ mask,
     TILE_LOOP_END
 }
 
+__global__ void k_to_float(const double* __restrict__ src, float* __restrict__ dst, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
+cudaError_t launch_to_float(Handle& H, const double* src, float* dst, long long n) {
+    k_to_float<<<H.target_blocks, kBlock, 0, H.stream>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_flags(Handle& H) {
     k_flags<<<tile_grid(H), tile_block(), 0, H.stream>>>(H.g, H.mask, H.flags, H.dctl, H.partials);
     return cudaGetLastError();

@@ -28,6 +28,9 @@ struct Handle {
     // outer Schur CG (cell space)
     double *op = nullptr, *orr = nullptr, *od = nullptr, *oq = nullptr, *og = nullptr;
     double* u = nullptr;         // recovered velocity [d][stride]
+    // FP32 inner solves of the mixed-precision path (allocated on first use)
+    float *axf = nullptr, *arf = nullptr, *apf = nullptr, *aqf = nullptr;
+    float *sxf = nullptr, *srf = nullptr, *spf = nullptr, *sqf = nullptr, *invdSf = nullptr;
     // connected fluid components (connectivity through unknown faces)
     int* cmp = nullptr;          // [ncell] component id, -1 on solid cells
     double* cmean = nullptr;     // [n_comp] per-component mean of the last projected vector
@@ -42,8 +45,8 @@ struct Handle {
     Ctl* dctl = nullptr;         // device control block
     Ctl* hctl = nullptr;         // pinned host shadow
 
-    cudaGraph_t graph_solve[2] = {nullptr, nullptr};
-    cudaGraphExec_t exec_solve[2] = {nullptr, nullptr};
+    cudaGraph_t graph_solve[4] = {nullptr, nullptr, nullptr, nullptr};      // [precision][precond]
+    cudaGraphExec_t exec_solve[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaGraph_t graph_recover = nullptr;
     cudaGraphExec_t exec_recover = nullptr;
     cudaGraph_t graph_solo = nullptr;
@@ -57,6 +60,7 @@ struct Handle {
     double last_tolA = 1e-12;
     int last_max_inner = 20000;
     int last_loop = 0;
+    int last_precision = 0;
     long long bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
@@ -68,9 +72,10 @@ cudaError_t launch_apply_A(Handle& H, const double* x, double* y);
 cudaError_t launch_apply_B(Handle& H, const double* u, double* p);
 cudaError_t launch_apply_BT(Handle& H, const double* p, double* u);
 cudaError_t launch_apply_simple(Handle& H, const double* p, double* q);
+cudaError_t launch_to_float(Handle& H, const double* src, float* dst, long long n);
 
 // krylov.cu: record the control flow of a call into R (graph nodes or direct launches)
-void record_solve(Handle& H, Recorder& R, int precond);
+void record_solve(Handle& H, Recorder& R, int precond, int precision);
 void record_recover(Handle& H, Recorder& R);
 void record_solve_A(Handle& H, Recorder& R, const double* b, double* x);
 cudaError_t time_kernel(Handle& H, int which, int slot, float* ms);

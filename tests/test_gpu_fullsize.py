@@ -54,3 +54,18 @@ def test_fullsize_against_recorded_oracle(workload, n, pc):
             assert np.linalg.norm(div) <= 1e-7 * np.linalg.norm(abs(prob.B) @ np.abs(u))
             res = prob.A @ u - (mac.force(geo, (1.0, 0.0, 0.0)) - prob.BT @ p)
             assert np.linalg.norm(res) <= 1e-9 * np.linalg.norm(prob.A @ u)
+
+
+@pytest.mark.parametrize("workload,n", [("spheres64", 64), ("spheres128", 128)])
+@pytest.mark.parametrize("pc", ["uzawa", "simple"])
+def test_fullsize_mixed_precision(workload, n, pc):
+    """Mixed precision at full size: permeability within 1e-6 of the FP64 oracle record."""
+    ref = _golden(workload, pc)
+    torch.cuda.set_device(0)
+    mask = synth.sphere_packing(n, 4.0, 8.0, 0.40, 0)
+    with binding.Geometry(mask) as g:
+        g.set_force((1.0, 0.0, 0.0))
+        st = g.solve(precond=PRECONDS[pc], precision=binding.MIXED, tol=1e-8)
+        assert st.status == binding.SCHUR_OK and st.rel_res < 1e-8
+        g.recover_velocity()
+        assert abs(g.permeability(0) - ref["k"][0]) <= 1e-6 * abs(ref["k"][0])

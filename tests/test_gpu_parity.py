@@ -249,3 +249,44 @@ def test_repeat_solves_are_deterministic(cuda):
             g.recover_velocity()
             out.append((g.field(binding.FIELD_P).clone(), g.permeability(0)))
         assert torch.equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+
+
+@pytest.mark.parametrize("precond", [binding.UZAWA, binding.SIMPLE])
+@pytest.mark.parametrize("name,force", [("squares2d", (1.0, 0.0)), ("spheres24", (1.0, 0.0, 0.0)),
+                                        ("rand3d_ragged", (0.0, 0.0, 1.0)),
+                                        ("spheres_ragged", (0.0, 1.0, 0.0))])
+def test_mixed_precision_against_fp64_oracle(cuda, name, force, precond):
+    """FP32 inner solves inside FP64 flexible CG + FP64 defect correction: the FP64 true
+    residual meets the tolerance and k is within 1e-6 of the FP64 oracle."""
+    mask, per, geo, g = _pair(name)
+    ref = stokes.solve(mask, force, stokes.Options(precond=precond, tol=1e-9), per)
+    g.set_force(force)
+    st = g.solve(precond=precond, precision=binding.MIXED, tol=1e-9)
+    assert st.status == binding.SCHUR_OK and st.rel_res < 1e-9
+    assert st.inner_iters_A_f32 > 0 and st.refinements >= 1
+    if precond == binding.SIMPLE:
+        assert st.inner_iters_S_f32 > 0 and st.inner_iters_S == 0
+    g.recover_velocity()
+    u = face_device_to_compact(g, geo, g.field(binding.FIELD_U))
+    assert np.linalg.norm(u - ref["u"]) <= 1e-6 * np.linalg.norm(ref["u"])
+    for a in range(geo.d):
+        assert abs(g.permeability(a) - ref["k"][a]) <= 1e-6 * abs(ref["k"][a]) + 1e-9 * geo.h ** 2
+    g.close()
+
+
+def test_mixed_zero_rhs_and_loop_modes(cuda):
+    """Mixed precision on the x-invariant channel (g = 0) returns the closed form, and the
+    host-driven loops give the graph's bits."""
+    with binding.Geometry(synth.channel_2d(32)) as g:
+        st = g.solve(precision=binding.MIXED, tol=1e-10)
+        assert st.zero_rhs == 1 and st.outer_iters == 0
+        g.recover_velocity()
+        assert abs(g.permeability(0) - 2255 / 32768) <= 1e-12 * 2255 / 32768
+    mask = synth.sphere_packing(20, 2.0, 4.0, 0.45, seed=9)
+    out = []
+    for mode in (binding.LOOP_GRAPH, binding.LOOP_HOST):
+        with binding.Geometry(mask) as g:
+            st = g.solve(precond=binding.SIMPLE, precision=binding.MIXED, tol=1e-8, loop_mode=mode)
+            out.append((st.outer_iters, st.refinements, st.inner_iters_A_f32,
+                        g.field(binding.FIELD_P).clone()))
+    assert out[0][:3] == out[1][:3] and torch.equal(out[0][3], out[1][3])
