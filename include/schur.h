@@ -61,6 +61,8 @@ enum { SCHUR_FIELD_P = 0, SCHUR_FIELD_U = 1, SCHUR_FIELD_FLAGS = 2, SCHUR_FIELD_
 enum { SCHUR_DTYPE_U8 = 0, SCHUR_DTYPE_F32 = 1, SCHUR_DTYPE_F64 = 2 };
 
 typedef struct schur_geom* schur_geom_t;
+typedef struct schur_batch* schur_batch_t;
+typedef struct schur_server* schur_server_t;
 
 /* Solver options.  Defaults (schur_opts_default): SIMPLE, unpreconditioned stop,
  * FP64, graph loop, tol 1e-8, tol_inner_A = tol_inner_S = 1e-12, max_outer 2000,
@@ -137,6 +139,15 @@ int schur_set_force(schur_geom_t g, const double f[3]);
  * is kept), or SCHUR_EINVAL / SCHUR_ECUDA. */
 int schur_solve(schur_geom_t g, const schur_opts* opts, schur_stats* stats);
 
+/* Asynchronous solve + velocity recovery + permeability (graph mode only): one graph
+ * launch on the handle's stream, returns at once.  schur_query tells whether it ended;
+ * schur_finish waits, fills the stats of the solve and of the recovery (either may be
+ * NULL) and returns the solve's status (or the recovery's when the solve succeeded).
+ * Other calls on the handle return SCHUR_ESTATE while the solve is in flight. */
+int schur_solve_async(schur_geom_t g, const schur_opts* opts);
+int schur_query(schur_geom_t g, int* done);
+int schur_finish(schur_geom_t g, schur_stats* solve_stats, schur_stats* recover_stats);
+
 /* Velocity recovery A u = f - B^T p (eq. velocity_schur) with the options of the last
  * schur_solve.  SCHUR_ESTATE before any solve. */
 int schur_recover_velocity(schur_geom_t g, schur_stats* stats);
@@ -194,6 +205,50 @@ int schur_time_kernel(schur_geom_t g, int kernel, float* ms);
 int schur_permeability_noalloc(const double* u, const uint8_t* flags, int ndim,
                                const int64_t dims[3], int64_t face_stride, void* stream,
                                double* k_dev);
+
+/* ---- batched execution -------------------------------------------------------------
+ * The solve + recovery of n geometries recorded as n parallel branches of ONE CUDA graph
+ * (one cudaGraphLaunch runs all of them; the GPU overlaps the branches).  The handles
+ * must stay alive and are used on `stream`; blocks_per_sm (1..32) sets the grid of
+ * every kernel to blocks_per_sm x SMs.  schur_batch_run launches the graph, waits, and
+ * fills n solve / recovery stats and 3n permeabilities (each output may be NULL); it
+ * returns the worst status.  schur_batch_autotune times the batch for blocks_per_sm in
+ * {2, 4, 8, 16} and leaves the geometries on the fastest. */
+int schur_batch_create(schur_geom_t* geoms, int n, const schur_opts* opts, int blocks_per_sm,
+                       void* stream, schur_batch_t* out);
+int schur_batch_run(schur_batch_t b, schur_stats* solve_stats, schur_stats* recover_stats,
+                    double* k_out);
+int schur_batch_autotune(schur_geom_t* geoms, int n, const schur_opts* opts, void* stream,
+                         int* best_blocks_per_sm, double* best_ms);
+void schur_batch_destroy(schur_batch_t b);
+
+/* ---- serving --------------------------------------------------------------------------
+ * A request loop driven by the caller: schur_server_submit queues a permeability job
+ * (host mask copied; unit force along `axis`); schur_server_progress admits queued jobs in
+ * arrival order while their estimated device footprint (schur_footprint_bytes) fits the
+ * budget and fewer than max_active run, launches each on its own stream (geometry +
+ * asynchronous solve + recovery), and collects finished ones without blocking;
+ * schur_server_take returns finished results.  Times are seconds since creation. */
+typedef struct {
+    int64_t id;
+    int status;
+    int outer_iters;
+    int64_t inner_iters;
+    double k;                    /* permeability along the job's axis */
+    double t_submit, t_start, t_done;
+    int64_t bytes;               /* footprint charged to the budget */
+} schur_job_result;
+
+int64_t schur_footprint_bytes(int ndim, const int64_t dims[3], int precision);
+int schur_server_create(const schur_opts* opts, int64_t mem_budget_bytes, int max_active,
+                        schur_server_t* out);
+int schur_server_submit(schur_server_t s, const uint8_t* host_mask, int ndim,
+                        const int64_t dims[3], const int periodic[3], int axis,
+                        int64_t* job_id);
+int schur_server_progress(schur_server_t s, int* n_active, int* n_pending);
+int schur_server_take(schur_server_t s, schur_job_result* out, int max, int* n_out);
+int schur_server_info(schur_server_t s, int64_t* peak_bytes, int* peak_active);
+void schur_server_destroy(schur_server_t s);
 
 /* Release the handle and all its device memory (NULL is ignored). */
 void schur_destroy(schur_geom_t g);

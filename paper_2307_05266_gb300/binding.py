@@ -28,7 +28,11 @@ EXPORTED = [
     "schur_recover_velocity", "schur_permeability", "schur_get_field",
     "schur_geometry_info", "schur_apply_A", "schur_apply_B", "schur_apply_BT",
     "schur_apply_simple", "schur_solve_A", "schur_time_kernel", "schur_destroy",
-    "schur_last_error", "schur_permeability_noalloc",
+    "schur_last_error", "schur_permeability_noalloc", "schur_solve_async", "schur_query",
+    "schur_finish", "schur_batch_create", "schur_batch_run", "schur_batch_autotune",
+    "schur_batch_destroy", "schur_footprint_bytes", "schur_server_create",
+    "schur_server_submit", "schur_server_progress", "schur_server_take", "schur_server_info",
+    "schur_server_destroy",
 ]
 KERNELS = {"cgA_dir": 0, "cgA_matvec": 1, "cgA_update": 2, "cgS_dir": 3, "cgS_matvec": 4,
            "cgS_update": 5, "cgA_dir_f32": 6, "cgA_matvec_f32": 7, "cgA_update_f32": 8,
@@ -50,6 +54,15 @@ class Stats(C.Structure):
                 ("rel_res_precond", C.c_double), ("g_norm", C.c_double),
                 ("kernel_launches", C.c_longlong), ("inner_iters_A_f32", C.c_longlong),
                 ("inner_iters_S_f32", C.c_longlong), ("refinements", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class JobResult(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int), ("outer_iters", C.c_int),
+                ("inner_iters", C.c_int64), ("k", C.c_double), ("t_submit", C.c_double),
+                ("t_start", C.c_double), ("t_done", C.c_double), ("bytes", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -94,6 +107,24 @@ def load(build_if_missing: bool = True):
         "schur_solve_A": (C.c_int, [vp, vp, vp, C.c_double, C.c_int, C.POINTER(C.c_int)]),
         "schur_time_kernel": (C.c_int, [vp, C.c_int, C.POINTER(C.c_float)]),
         "schur_permeability_noalloc": (C.c_int, [vp, vp, C.c_int, i64p, C.c_int64, vp, vp]),
+        "schur_solve_async": (C.c_int, [vp, C.POINTER(Opts)]),
+        "schur_query": (C.c_int, [vp, C.POINTER(C.c_int)]),
+        "schur_finish": (C.c_int, [vp, C.POINTER(Stats), C.POINTER(Stats)]),
+        "schur_batch_create": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(Opts), C.c_int, vp,
+                                         C.POINTER(vp)]),
+        "schur_batch_run": (C.c_int, [vp, C.POINTER(Stats), C.POINTER(Stats),
+                                      C.POINTER(C.c_double)]),
+        "schur_batch_autotune": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(Opts), vp,
+                                           C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+        "schur_batch_destroy": (None, [vp]),
+        "schur_footprint_bytes": (C.c_int64, [C.c_int, i64p, C.c_int]),
+        "schur_server_create": (C.c_int, [C.POINTER(Opts), C.c_int64, C.c_int, C.POINTER(vp)]),
+        "schur_server_submit": (C.c_int, [vp, vp, C.c_int, i64p, C.POINTER(C.c_int), C.c_int,
+                                          C.POINTER(C.c_int64)]),
+        "schur_server_progress": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "schur_server_take": (C.c_int, [vp, C.POINTER(JobResult), C.c_int, C.POINTER(C.c_int)]),
+        "schur_server_info": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
+        "schur_server_destroy": (None, [vp]),
         "schur_destroy": (None, [vp]),
         "schur_last_error": (C.c_char_p, []),
     }
@@ -249,6 +280,20 @@ class Geometry:
     def apply_simple(self, p, q):
         _check(load().schur_apply_simple(self._h, _ptr(p), _ptr(q)))
 
+    def solve_async(self, **kw):
+        _check(load().schur_solve_async(self._h, C.byref(default_opts(**kw))))
+
+    def query(self):
+        d = C.c_int()
+        _check(load().schur_query(self._h, C.byref(d)))
+        return bool(d.value)
+
+    def finish(self, allow_fail=False):
+        st, rs = Stats(), Stats()
+        rc = load().schur_finish(self._h, C.byref(st), C.byref(rs))
+        _check(rc, (SCHUR_OK, SCHUR_ENOTCONV, SCHUR_EBREAKDOWN) if allow_fail else (SCHUR_OK,))
+        return st, rs
+
     def solve_A(self, b, x, tol=1e-12, max_iter=20000):
         it = C.c_int()
         _check(load().schur_solve_A(self._h, _ptr(b), _ptr(x), tol, max_iter, C.byref(it)))
@@ -283,3 +328,106 @@ class Geometry:
         """Face-space tensor [d*stride] -> [d, *shape] view (drops the padding)."""
         d, s, n = self.ndim, self.face_stride, self.n_cells
         return t.view(d, s)[:, :n].reshape((d,) + self.shape)
+
+
+def _dims(shape):
+    return (C.c_int64 * 3)(*(list(reversed(shape)) + [1] * (3 - len(shape))))
+
+
+def _per(periodic, ndim):
+    per = periodic if periodic is not None else (True,) * ndim
+    return (C.c_int * 3)(*([int(bool(p)) for p in per] + [1] * (3 - len(per))))
+
+
+class Batch:
+    """Many geometries solved by one CUDA graph launch (see schur_batch_create)."""
+
+    def __init__(self, geoms, blocks_per_sm=8, stream=None, **opts):
+        self.geoms = list(geoms)
+        self.opts = default_opts(**opts)
+        self.stream = geoms[0].stream if stream is None else stream
+        arr = (C.c_void_p * len(self.geoms))(*[g._h.value for g in self.geoms])
+        self._arr = arr
+        h = C.c_void_p()
+        _check(load().schur_batch_create(arr, len(self.geoms), C.byref(self.opts),
+                                         blocks_per_sm, C.c_void_p(self.stream), C.byref(h)))
+        self._h = h
+
+    @staticmethod
+    def autotune(geoms, stream=None, **opts):
+        o = default_opts(**opts)
+        arr = (C.c_void_p * len(geoms))(*[g._h.value for g in geoms])
+        best, ms = C.c_int(), C.c_double()
+        st = geoms[0].stream if stream is None else stream
+        _check(load().schur_batch_autotune(arr, len(geoms), C.byref(o), C.c_void_p(st),
+                                           C.byref(best), C.byref(ms)))
+        return best.value, ms.value
+
+    def run(self, allow_fail=False):
+        n = len(self.geoms)
+        ss, rs = (Stats * n)(), (Stats * n)()
+        k = (C.c_double * (3 * n))()
+        rc = load().schur_batch_run(self._h, ss, rs, k)
+        _check(rc, (SCHUR_OK, SCHUR_ENOTCONV, SCHUR_EBREAKDOWN) if allow_fail else (SCHUR_OK,))
+        return list(ss), list(rs), [tuple(k[3 * i:3 * i + 3]) for i in range(n)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().schur_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Request loop with admission by device footprint (see schur_server_create)."""
+
+    def __init__(self, mem_budget_bytes, max_active=16, **opts):
+        self.opts = default_opts(**opts)
+        h = C.c_void_p()
+        _check(load().schur_server_create(C.byref(self.opts), int(mem_budget_bytes),
+                                          int(max_active), C.byref(h)))
+        self._h = h
+
+    def submit(self, mask, axis=0, periodic=None):
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        jid = C.c_int64()
+        _check(load().schur_server_submit(self._h, m.ctypes.data_as(C.c_void_p), m.ndim,
+                                          _dims(m.shape), _per(periodic, m.ndim), axis,
+                                          C.byref(jid)))
+        return jid.value
+
+    def progress(self):
+        a, p = C.c_int(), C.c_int()
+        _check(load().schur_server_progress(self._h, C.byref(a), C.byref(p)))
+        return a.value, p.value
+
+    def take(self, max_results=1024):
+        out = (JobResult * max_results)()
+        n = C.c_int()
+        _check(load().schur_server_take(self._h, out, max_results, C.byref(n)))
+        return [out[i].as_dict() for i in range(n.value)]
+
+    def info(self):
+        b, a = C.c_int64(), C.c_int()
+        _check(load().schur_server_info(self._h, C.byref(b), C.byref(a)))
+        return {"peak_bytes": b.value, "peak_active": a.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().schur_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def footprint_bytes(shape, precision=FP64):
+    return load().schur_footprint_bytes(len(shape), _dims(shape), precision)

@@ -51,9 +51,13 @@ void free_all(Handle& H) {
     for (int k = 0; k < 4; ++k) {
         if (H.exec_solve[k]) cudaGraphExecDestroy(H.exec_solve[k]);
         if (H.graph_solve[k]) cudaGraphDestroy(H.graph_solve[k]);
-        H.exec_solve[k] = nullptr;
-        H.graph_solve[k] = nullptr;
+        if (H.exec_full[k]) cudaGraphExecDestroy(H.exec_full[k]);
+        if (H.graph_full[k]) cudaGraphDestroy(H.graph_full[k]);
+        H.exec_solve[k] = H.exec_full[k] = nullptr;
+        H.graph_solve[k] = H.graph_full[k] = nullptr;
     }
+    if (H.done_ev) cudaEventDestroy(H.done_ev);
+    H.done_ev = nullptr;
     if (H.exec_recover) cudaGraphExecDestroy(H.exec_recover);
     if (H.graph_recover) cudaGraphDestroy(H.graph_recover);
     if (H.exec_solo) cudaGraphExecDestroy(H.exec_solo);
@@ -224,7 +228,8 @@ void reset_call(Handle& H, int use_graph) {
     c->launches = 0;
     c->inner_status = 0;
     c->ticket = 0;
-    c->inA.total = c->inS.total = c->out.total = c->solo.total = 0;
+    c->inA.total = c->inS.total = c->out.total = c->solo.total = c->rec.total = 0;
+    c->inA32.total = c->inS32.total = 0;
 }
 
 int upload(Handle& H) {
@@ -249,6 +254,109 @@ int map_status(int st) {
 }  // namespace
 
 int schur_set_error_internal(int code, const char* msg) { return set_error(code, msg); }
+
+namespace schur {
+
+Handle& handle_of(schur_geom_t g) { return g->H; }
+
+int check_opts(const schur_opts& o) {
+    if (o.precond != SCHUR_UZAWA && o.precond != SCHUR_SIMPLE)
+        return set_error(SCHUR_EINVAL, "precond must be SCHUR_UZAWA or SCHUR_SIMPLE");
+    if (o.stop_norm != SCHUR_STOP_UNPRECOND && o.stop_norm != SCHUR_STOP_PRECOND)
+        return set_error(SCHUR_EINVAL, "bad stop_norm");
+    if (o.precision != SCHUR_FP64 && o.precision != SCHUR_MIXED)
+        return set_error(SCHUR_EINVAL, "precision must be SCHUR_FP64 or SCHUR_MIXED");
+    if (o.precision == SCHUR_MIXED &&
+        (!(o.tol_inner_f32 > 0) || !(o.refine_factor > 0 && o.refine_factor < 1) ||
+         o.max_refine < 1 || o.step_max < 1))
+        return set_error(SCHUR_EINVAL, "mixed precision needs tol_inner_f32 > 0, "
+                                       "0 < refine_factor < 1, max_refine >= 1, step_max >= 1");
+    if (o.loop_mode != SCHUR_LOOP_GRAPH && o.loop_mode != SCHUR_LOOP_HOST)
+        return set_error(SCHUR_EINVAL, "bad loop_mode");
+    if (!(o.tol > 0) || !(o.tol_inner_A > 0) || !(o.tol_inner_S > 0) || o.max_outer < 1 ||
+        o.max_inner < 1)
+        return set_error(SCHUR_EINVAL, "tolerances must be > 0 and caps >= 1");
+    return SCHUR_OK;
+}
+
+// Allocate what the options need and write them into the host control block (the
+// recovery's inner solve uses the same tolerance and cap as the solve's A solves).
+int prepare_solve(Handle& H, const schur_opts& o, int use_graph) {
+    if (o.precision == SCHUR_MIXED && !H.axf) {
+        // FP32 inner-solve buffers, allocated on the first mixed-precision solve
+        const size_t nf = (size_t)H.g.d * H.g.stride, nc = (size_t)H.g.ncell;
+        cudaError_t e = cudaSuccess;
+        auto A = [&](float** p, size_t n) { if (e == cudaSuccess) e = alloc(H, p, n); };
+        A(&H.axf, nf); A(&H.arf, nf); A(&H.apf, nf); A(&H.aqf, nf);
+        A(&H.sxf, nc); A(&H.srf, nc); A(&H.spf, nc); A(&H.sqf, nc); A(&H.invdSf, nc);
+        if (e == cudaSuccess) e = launch_to_float(H, H.invdS, H.invdSf, (long long)nc);
+        if (e == cudaErrorMemoryAllocation) return set_error(SCHUR_ENOMEM, "device allocation failed");
+        if (e != cudaSuccess) return cuda_error(e, "mixed-precision buffers");
+    }
+    Ctl* c = H.hctl;
+    reset_call(H, use_graph);
+    c->precond = o.precond;
+    c->stop_norm = o.stop_norm;
+    c->inA.tol = o.tol_inner_A;
+    c->inA.max_iter = o.max_inner;
+    c->rec.tol = o.tol_inner_A;
+    c->rec.max_iter = o.max_inner;
+    c->inS.tol = o.tol_inner_S;
+    c->inS.max_iter = o.max_inner;
+    c->out.tol = o.tol;
+    c->out.max_iter = o.max_outer;
+    c->inA32.tol = o.tol_inner_f32;
+    c->inA32.max_iter = o.max_inner;
+    c->inS32.tol = o.tol_inner_f32;
+    c->inS32.max_iter = o.max_inner;
+    c->mix.max_refine = o.max_refine;
+    c->mix.step_max = o.step_max;
+    c->mix.factor = o.refine_factor;
+    c->mix.refine = 0;
+    c->mix.stop = 0;
+    c->zero_rhs = 0;
+    H.last_loop = o.loop_mode;
+    H.last_precision = o.precision;
+    return SCHUR_OK;
+}
+
+int upload_ctl(Handle& H) { return upload(H); }
+
+int download_ctl_async(Handle& H) {
+    CUDA_TRY(cudaMemcpyAsync(H.hctl, H.dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, H.stream),
+             "control download");
+    return SCHUR_OK;
+}
+
+void fill_solve_stats(Handle& H, int precision, schur_stats* stats) {
+    const Ctl* c = H.hctl;
+    std::memset(stats, 0, sizeof(*stats));
+    stats->status = map_status(c->out.status);
+    stats->outer_iters = c->out.iter;
+    stats->zero_rhs = c->zero_rhs;
+    stats->inner_status = map_status(c->inner_status);
+    stats->inner_iters_A = c->inA.total;
+    stats->inner_iters_S = c->inS.total;
+    stats->rel_res = c->out.rel;
+    stats->rel_res_precond = c->out.relz;
+    stats->g_norm = std::sqrt(c->g_norm2);
+    stats->kernel_launches = c->launches;
+    stats->inner_iters_A_f32 = c->inA32.total;
+    stats->inner_iters_S_f32 = c->inS32.total;
+    stats->refinements = precision == SCHUR_MIXED ? c->mix.refine : 0;
+}
+
+void fill_recover_stats(Handle& H, schur_stats* stats) {
+    const Ctl* c = H.hctl;
+    std::memset(stats, 0, sizeof(*stats));
+    stats->status = map_status(c->rec.status);
+    stats->inner_status = map_status(c->inner_status);
+    stats->inner_iters_A = c->rec.total;
+    stats->rel_res = c->rec.rel;
+    stats->kernel_launches = c->launches;
+}
+
+}  // namespace schur
 
 extern "C" {
 
@@ -408,56 +516,11 @@ int schur_solve(schur_geom_t G, const schur_opts* opts, schur_stats* stats) {
     if (!G) return set_error(SCHUR_EINVAL, "null handle");
     schur_opts o;
     if (opts) o = *opts; else schur_opts_default(&o);
-    if (o.precond != SCHUR_UZAWA && o.precond != SCHUR_SIMPLE)
-        return set_error(SCHUR_EINVAL, "precond must be SCHUR_UZAWA or SCHUR_SIMPLE");
-    if (o.stop_norm != SCHUR_STOP_UNPRECOND && o.stop_norm != SCHUR_STOP_PRECOND)
-        return set_error(SCHUR_EINVAL, "bad stop_norm");
-    if (o.precision != SCHUR_FP64 && o.precision != SCHUR_MIXED)
-        return set_error(SCHUR_EINVAL, "precision must be SCHUR_FP64 or SCHUR_MIXED");
-    if (o.precision == SCHUR_MIXED &&
-        (!(o.tol_inner_f32 > 0) || !(o.refine_factor > 0 && o.refine_factor < 1) ||
-         o.max_refine < 1 || o.step_max < 1))
-        return set_error(SCHUR_EINVAL, "mixed precision needs tol_inner_f32 > 0, "
-                                       "0 < refine_factor < 1, max_refine >= 1, step_max >= 1");
-    if (o.loop_mode != SCHUR_LOOP_GRAPH && o.loop_mode != SCHUR_LOOP_HOST)
-        return set_error(SCHUR_EINVAL, "bad loop_mode");
-    if (!(o.tol > 0) || !(o.tol_inner_A > 0) || !(o.tol_inner_S > 0) || o.max_outer < 1 ||
-        o.max_inner < 1)
-        return set_error(SCHUR_EINVAL, "tolerances must be > 0 and caps >= 1");
     Handle& H = G->H;
-    if (o.precision == SCHUR_MIXED && !H.axf) {
-        // FP32 inner-solve buffers, allocated on the first mixed-precision solve
-        const size_t nf = (size_t)H.g.d * H.g.stride, nc = (size_t)H.g.ncell;
-        cudaError_t e = cudaSuccess;
-        auto A = [&](float** p, size_t n) { if (e == cudaSuccess) e = alloc(H, p, n); };
-        A(&H.axf, nf); A(&H.arf, nf); A(&H.apf, nf); A(&H.aqf, nf);
-        A(&H.sxf, nc); A(&H.srf, nc); A(&H.spf, nc); A(&H.sqf, nc); A(&H.invdSf, nc);
-        if (e == cudaSuccess) e = launch_to_float(H, H.invdS, H.invdSf, (long long)nc);
-        if (e == cudaErrorMemoryAllocation) return set_error(SCHUR_ENOMEM, "device allocation failed");
-        if (e != cudaSuccess) return cuda_error(e, "mixed-precision buffers");
-    }
-    Ctl* c = H.hctl;
-    reset_call(H, o.loop_mode == SCHUR_LOOP_GRAPH);
-    c->precond = o.precond;
-    c->stop_norm = o.stop_norm;
-    c->inA.tol = o.tol_inner_A;
-    c->inA.max_iter = o.max_inner;
-    c->inS.tol = o.tol_inner_S;
-    c->inS.max_iter = o.max_inner;
-    c->out.tol = o.tol;
-    c->out.max_iter = o.max_outer;
-    c->inA32.tol = o.tol_inner_f32;
-    c->inA32.max_iter = o.max_inner;
-    c->inS32.tol = o.tol_inner_f32;
-    c->inS32.max_iter = o.max_inner;
-    c->inA32.total = c->inS32.total = 0;
-    c->mix.max_refine = o.max_refine;
-    c->mix.step_max = o.step_max;
-    c->mix.factor = o.refine_factor;
-    c->mix.refine = 0;
-    c->mix.stop = 0;
-    c->zero_rhs = 0;
-    int rc;
+    if (H.pending) return set_error(SCHUR_ESTATE, "an asynchronous solve is in flight");
+    int rc = check_opts(o);
+    if (rc) return rc;
+    if ((rc = prepare_solve(H, o, o.loop_mode == SCHUR_LOOP_GRAPH))) return rc;
     const int gi = o.precision * 2 + o.precond;
     if (o.loop_mode == SCHUR_LOOP_GRAPH) {
         rc = build_graph(H, &H.graph_solve[gi], &H.exec_solve[gi],
@@ -475,26 +538,8 @@ int schur_solve(schur_geom_t G, const schur_opts* opts, schur_stats* stats) {
     if ((rc = download(H))) return rc;
     H.solved = true;
     H.recovered = false;
-    H.last_tolA = o.tol_inner_A;
-    H.last_max_inner = o.max_inner;
-    H.last_loop = o.loop_mode;
-    H.last_precision = o.precision;
-    if (stats) {
-        stats->status = map_status(c->out.status);
-        stats->outer_iters = c->out.iter;
-        stats->zero_rhs = c->zero_rhs;
-        stats->inner_status = map_status(c->inner_status);
-        stats->inner_iters_A = c->inA.total;
-        stats->inner_iters_S = c->inS.total;
-        stats->rel_res = c->out.rel;
-        stats->rel_res_precond = c->out.relz;
-        stats->g_norm = std::sqrt(c->g_norm2);
-        stats->kernel_launches = c->launches;
-        stats->inner_iters_A_f32 = c->inA32.total;
-        stats->inner_iters_S_f32 = c->inS32.total;
-        stats->refinements = o.precision == SCHUR_MIXED ? c->mix.refine : 0;
-    }
-    const int st = map_status(c->out.status);
+    if (stats) fill_solve_stats(H, o.precision, stats);
+    const int st = map_status(H.hctl->out.status);
     if (st != SCHUR_OK) set_error(st, "outer iteration did not converge");
     return st;
 }
@@ -502,11 +547,9 @@ int schur_solve(schur_geom_t G, const schur_opts* opts, schur_stats* stats) {
 int schur_recover_velocity(schur_geom_t G, schur_stats* stats) {
     if (!G) return set_error(SCHUR_EINVAL, "null handle");
     Handle& H = G->H;
+    if (H.pending) return set_error(SCHUR_ESTATE, "an asynchronous solve is in flight");
     if (!H.solved) return set_error(SCHUR_ESTATE, "recover_velocity needs a schur_solve first");
-    Ctl* c = H.hctl;
     reset_call(H, H.last_loop == SCHUR_LOOP_GRAPH);
-    c->inA.tol = H.last_tolA;
-    c->inA.max_iter = H.last_max_inner;
     int rc;
     if (H.last_loop == SCHUR_LOOP_GRAPH) {
         rc = build_graph(H, &H.graph_recover, &H.exec_recover,
@@ -523,16 +566,60 @@ int schur_recover_velocity(schur_geom_t G, schur_stats* stats) {
     }
     if ((rc = download(H))) return rc;
     H.recovered = true;
-    if (stats) {
-        std::memset(stats, 0, sizeof(*stats));
-        stats->status = map_status(c->inA.status);
-        stats->inner_status = map_status(c->inner_status);
-        stats->inner_iters_A = c->inA.total;
-        stats->rel_res = c->inA.rel;
-        stats->kernel_launches = c->launches;
-    }
-    const int st = map_status(c->inA.status);
+    if (stats) fill_recover_stats(H, stats);
+    const int st = map_status(H.hctl->rec.status);
     if (st != SCHUR_OK) set_error(st, "velocity recovery did not converge");
+    return st;
+}
+
+int schur_solve_async(schur_geom_t G, const schur_opts* opts) {
+    if (!G) return set_error(SCHUR_EINVAL, "null handle");
+    schur_opts o;
+    if (opts) o = *opts; else schur_opts_default(&o);
+    o.loop_mode = SCHUR_LOOP_GRAPH;
+    Handle& H = G->H;
+    if (H.pending) return set_error(SCHUR_ESTATE, "an asynchronous solve is in flight");
+    int rc = check_opts(o);
+    if (rc) return rc;
+    if ((rc = prepare_solve(H, o, 1))) return rc;
+    const int gi = o.precision * 2 + o.precond;
+    rc = build_graph(H, &H.graph_full[gi], &H.exec_full[gi],
+                     [&](Recorder& R) { record_solve_recover(H, R, o.precond, o.precision); });
+    if (rc) return rc;
+    if (!H.done_ev) CUDA_TRY(cudaEventCreateWithFlags(&H.done_ev, cudaEventDisableTiming), "event");
+    if ((rc = upload(H))) return rc;
+    CUDA_TRY(cudaGraphLaunch(H.exec_full[gi], H.stream), "cudaGraphLaunch");
+    if ((rc = download_ctl_async(H))) return rc;
+    CUDA_TRY(cudaEventRecord(H.done_ev, H.stream), "event record");
+    H.pending = true;
+    H.pending_precision = o.precision;
+    H.solved = H.recovered = false;
+    return SCHUR_OK;
+}
+
+int schur_query(schur_geom_t G, int* done) {
+    if (!G || !done) return set_error(SCHUR_EINVAL, "null argument");
+    Handle& H = G->H;
+    if (!H.pending) { *done = 1; return SCHUR_OK; }
+    cudaError_t e = cudaEventQuery(H.done_ev);
+    if (e == cudaErrorNotReady) { *done = 0; return SCHUR_OK; }
+    if (e != cudaSuccess) return cuda_error(e, "event query");
+    *done = 1;
+    return SCHUR_OK;
+}
+
+int schur_finish(schur_geom_t G, schur_stats* solve_stats, schur_stats* recover_stats) {
+    if (!G) return set_error(SCHUR_EINVAL, "null handle");
+    Handle& H = G->H;
+    if (!H.pending) return set_error(SCHUR_ESTATE, "no asynchronous solve in flight");
+    CUDA_TRY(cudaEventSynchronize(H.done_ev), "event synchronize");
+    H.pending = false;
+    H.solved = H.recovered = true;
+    if (solve_stats) fill_solve_stats(H, H.pending_precision, solve_stats);
+    if (recover_stats) fill_recover_stats(H, recover_stats);
+    int st = map_status(H.hctl->out.status);
+    if (st == SCHUR_OK) st = map_status(H.hctl->rec.status);
+    if (st != SCHUR_OK) set_error(st, "solve or recovery did not converge");
     return st;
 }
 

@@ -23,7 +23,7 @@ constexpr int kTileY = 8;              // rows of a stencil tile
 constexpr int kBlock = kTileX * kTileY;
 constexpr int kMaxRed = 4;             // doubles reduced by one kernel at most
 constexpr int kMaxBlocks = 4096;       // grid cap of every reducing kernel
-constexpr int kSlots = 32;             // loop-condition slots per handle
+constexpr int kSlots = 256;            // loop-condition slots per handle
 constexpr double kZeroRhsRtol = 1e-12; // g == 0 when ||g|| <= this * || |B| |u| ||
 constexpr int kMaxBig = 8;             // fluid components reduced by the full grid
 constexpr long long kBigMin = 2048;    // smallest component treated as "big"
@@ -102,7 +102,7 @@ struct Ctl {
     unsigned long long handle[kSlots];
     unsigned int cond[kSlots];
     // Krylov instances
-    CgState inA, inS, out, solo, inA32, inS32;
+    CgState inA, inS, out, solo, inA32, inS32, rec;
     Mix mix;
     // results
     double g_norm2, g_scale2;

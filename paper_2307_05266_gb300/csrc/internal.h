@@ -7,6 +7,7 @@
 #include <utility>
 #include <vector>
 
+#include "../../include/schur.h"
 #include "common.cuh"
 
 namespace schur {
@@ -51,6 +52,11 @@ struct Handle {
     cudaGraphExec_t exec_recover = nullptr;
     cudaGraph_t graph_solo = nullptr;
     cudaGraphExec_t exec_solo = nullptr;
+    cudaGraph_t graph_full[4] = {nullptr, nullptr, nullptr, nullptr};  // solve + recover
+    cudaGraphExec_t exec_full[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t done_ev = nullptr;    // end of an asynchronous solve
+    bool pending = false;             // an asynchronous solve is in flight
+    int pending_precision = 0;
     int next_slot = 0;
     std::vector<std::pair<int, unsigned long long>> handles;
 
@@ -77,6 +83,7 @@ cudaError_t launch_to_float(Handle& H, const double* src, float* dst, long long 
 // krylov.cu: record the control flow of a call into R (graph nodes or direct launches)
 void record_solve(Handle& H, Recorder& R, int precond, int precision);
 void record_recover(Handle& H, Recorder& R);
+void record_solve_recover(Handle& H, Recorder& R, int precond, int precision);
 void record_solve_A(Handle& H, Recorder& R, const double* b, double* x);
 cudaError_t time_kernel(Handle& H, int which, int slot, float* ms);
 
@@ -84,3 +91,15 @@ cudaError_t time_kernel(Handle& H, int which, int slot, float* ms);
 
 // api.cu: record an error for schur_last_error() and return `code`
 int schur_set_error_internal(int code, const char* msg);
+
+// api.cu: pieces of a solve shared by the synchronous, asynchronous, batched and served
+// paths.
+namespace schur {
+int check_opts(const schur_opts& o);
+int prepare_solve(Handle& H, const schur_opts& o, int use_graph);
+int upload_ctl(Handle& H);
+int download_ctl_async(Handle& H);
+void fill_solve_stats(Handle& H, int precision, schur_stats* stats);
+void fill_recover_stats(Handle& H, schur_stats* stats);
+Handle& handle_of(schur_geom_t g);
+}  // namespace schur

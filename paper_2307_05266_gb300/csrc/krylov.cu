@@ -1122,10 +1122,15 @@ void record_solve(Handle& H, Recorder& R, int precond, int precision) {
     else record_solve_fp64(H, R, precond);
 }
 
+void record_solve_recover(Handle& H, Recorder& R, int precond, int precision) {
+    record_solve(H, R, precond, precision);
+    record_recover(H, R);
+}
+
 void record_recover(Handle& H, Recorder& R) {
     Ctl* ctl = H.dctl;
     const int s = R.new_slot();
-    record_A_solve<double>(H, R, innerA64(H), &ctl->inA, s, H.op, -1.0, 1.0, nullptr);
+    record_A_solve<double>(H, R, innerA64(H), &ctl->rec, s, H.op, -1.0, 1.0, nullptr);
     const long long nf = (long long)H.g.d * H.g.stride;
     R.launch("copy_u", k_copy_u, sgrid(H, nf), sblock(), H.g, (const uint8_t*)H.flags,
              (const double*)H.ax, H.u, ctl, H.partials);

@@ -1,0 +1,129 @@
+"""Asynchronous, batched and served execution: each result equals the same job run alone.
+
+Kernels use a fixed grid per geometry and deterministic reductions, so a job gives the
+same bits whether it runs alone, inside one batch graph with other geometries, or
+interleaved with other requests in the server (the stated tolerance is 1e-6 in k for
+the mixed-precision path; bitwise equality is checked where the launch shape is equal).
+"""
+
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2307_05266_gb300 import binding, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _masks():
+    specs = [(24, 2.0, 4.0, 0.45, 1), (32, 3.0, 6.0, 0.35, 2), (20, 2.0, 3.0, 0.5, 3),
+             (28, 2.0, 5.0, 0.3, 4), (36, 3.0, 7.0, 0.4, 5), ((32, 24, 20), 2.0, 4.0, 0.45, 6)]
+    return [synth.sphere_packing(n, a, b, phi, s) for n, a, b, phi, s in specs]
+
+
+def _alone(mask, axis, **opts):
+    f = [0.0, 0.0, 0.0]
+    f[axis] = 1.0
+    with binding.Geometry(mask) as g:
+        g.set_force(f)
+        st = g.solve(**opts)
+        rs = g.recover_velocity()
+        return st.outer_iters, st.inner_iters_A + st.inner_iters_A_f32, g.permeability(axis)
+
+
+def test_async_equals_sync():
+    torch.cuda.set_device(0)
+    mask = _masks()[0]
+    ref = _alone(mask, 0, precond=binding.SIMPLE)
+    with binding.Geometry(mask) as g:
+        g.solve_async(precond=binding.SIMPLE)
+        while not g.query():
+            time.sleep(0.001)
+        st, rs = g.finish()
+        assert (st.outer_iters, st.inner_iters_A) == ref[:2]
+        assert g.permeability(0) == ref[2]
+        assert rs.inner_iters_A > 0
+
+
+@pytest.mark.parametrize("precision", [binding.FP64, binding.MIXED])
+def test_batch_equals_individual(precision):
+    torch.cuda.set_device(0)
+    masks = _masks()
+    refs = [_alone(m, 0, precond=binding.SIMPLE, precision=precision, tol=1e-8) for m in masks]
+    geoms = [binding.Geometry(m) for m in masks]
+    b = binding.Batch(geoms, blocks_per_sm=8, precond=binding.SIMPLE, precision=precision,
+                      tol=1e-8)
+    for _ in range(2):                      # the batch graph can be relaunched
+        ss, rs, ks = b.run()
+        for i, ref in enumerate(refs):
+            assert ss[i].outer_iters == ref[0]
+            assert ks[i][0] == ref[2]
+    b.close()
+    for g in geoms:
+        g.close()
+
+
+def test_batch_autotune_keeps_results():
+    torch.cuda.set_device(0)
+    masks = _masks()
+    refs = [_alone(m, 0, precond=binding.UZAWA, precision=binding.MIXED, tol=1e-8) for m in masks]
+    geoms = [binding.Geometry(m) for m in masks]
+    best, ms = binding.Batch.autotune(geoms, precond=binding.UZAWA, precision=binding.MIXED,
+                                      tol=1e-8)
+    assert best in (2, 4, 8, 16) and ms > 0
+    b = binding.Batch(geoms, blocks_per_sm=best, precond=binding.UZAWA,
+                      precision=binding.MIXED, tol=1e-8)
+    ss, rs, ks = b.run()
+    for i, ref in enumerate(refs):
+        assert abs(ks[i][0] - ref[2]) <= 1e-6 * abs(ref[2])
+    b.close()
+    for g in geoms:
+        g.close()
+
+
+def _serve(masks, axes, budget, max_active, **opts):
+    srv = binding.Server(budget, max_active=max_active, **opts)
+    ids = [srv.submit(m, axis=a) for m, a in zip(masks, axes)]
+    res = {}
+    t0 = time.time()
+    while len(res) < len(ids):
+        srv.progress()
+        for r in srv.take():
+            res[r["id"]] = r
+        assert time.time() - t0 < 300
+        time.sleep(0.0005)
+    info = srv.info()
+    srv.close()
+    return [res[i] for i in ids], info
+
+
+def test_server_results_alone_equal_in_mix():
+    """Continuous batching: every job's permeability is the same when it runs alone
+    (one job at a time) and when it overlaps with the others."""
+    torch.cuda.set_device(0)
+    masks = _masks()
+    axes = [0, 1, 2, 0, 1, 2]
+    opts = dict(precond=binding.SIMPLE, precision=binding.MIXED, tol=1e-8)
+    alone, _ = _serve(masks, axes, 1 << 36, 1, **opts)
+    mixed, info = _serve(masks, axes, 1 << 36, 6, **opts)
+    assert info["peak_active"] > 1
+    for a, m in zip(alone, mixed):
+        assert a["status"] == binding.SCHUR_OK and m["status"] == binding.SCHUR_OK
+        assert a["k"] == m["k"] and a["outer_iters"] == m["outer_iters"]
+    for mask, ax, r in zip(masks, axes, mixed):
+        ref = _alone(mask, ax, **opts)
+        assert abs(r["k"] - ref[2]) <= 1e-6 * abs(ref[2])
+
+
+def test_server_admission_respects_budget():
+    torch.cuda.set_device(0)
+    masks = _masks()
+    need = max(binding.footprint_bytes(m.shape, binding.MIXED) for m in masks)
+    budget = int(2.5 * need)                # at most two of the largest at a time
+    res, info = _serve(masks, [0] * len(masks), budget, 16, precision=binding.MIXED)
+    assert info["peak_bytes"] <= budget
+    assert all(r["status"] == binding.SCHUR_OK for r in res)
+    # waiting jobs start only after earlier ones free memory
+    assert all(r["t_start"] >= r["t_submit"] for r in res)
