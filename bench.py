@@ -1,24 +1,28 @@
 """Benchmark of the GB300 Schur-complement Stokes path.
 
-One step = create_geometry (mask -> face flags, components) followed, for Uzawa and for
-SIMPLE, by schur_solve (Algorithm 1 to tol 1e-8, inner tolerances 1e-12), velocity
-recovery and the permeability read-back: two Schur solves per step on the workload
-"spheres128" (128^3 periodic overlapping spheres, radii U[4,8), porosity 0.40, seed 0,
-f = e_x, FP64).
+Headline step = create_geometry (mask -> face flags, components, work lists) followed,
+for Uzawa and for SIMPLE, by schur_solve (Algorithm 1 to tol 1e-8, inner tolerances
+1e-12, FP64), velocity recovery and the permeability read-back: two Schur solves per step
+on "spheres128" (128^3 periodic overlapping spheres, radii U[4,8), porosity 0.40, seed 0,
+f = e_x).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--patterns mixed,batch,serve|none]
 
-Prints one JSON line.  value = Schur solves per second on the device-resident mask;
-e2e = the same with the mask in host memory (its H2D copy and the permeability D2H
-inside the timed region).  --impl reference times the FP64 CPU oracle on a bounded
-sample of the same workload and scales it to whole solves with the oracle's own
-iteration counts.
+Prints one JSON line.  value = Schur solves per second with the mask resident on the
+device; e2e = the same with the mask in host memory (H2D copy and permeability D2H inside
+the timed region).  After the timed region (N = 1 only) the line also reports the
+mixed-precision solves of the same workload, a batch of 64 uneven packings solved by one
+graph launch, and a Poisson-arrival serving run with p50/p99 latency.  --impl reference
+times the FP64 CPU oracle on a bounded sample of the same workload and scales it to whole
+solves with the oracle's own recorded iteration counts.
 """
 
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -35,16 +39,27 @@ WORKLOAD = dict(name="spheres128", n=128, r_min=4.0, r_max=8.0, porosity=0.40, s
 DESC = ("spheres128: 128^3 periodic overlapping solid spheres, radii U[4,8), porosity "
         "0.40, seed 0 (+rank), f = e_x, FP64; Uzawa and SIMPLE Schur-CG to 1e-8 "
         "(unpreconditioned), inner Jacobi-PCG to 1e-12")
-W_BYTES = 8
-# algorithmic bytes per unknown (face kernels) or per fluid cell (cell kernels), FP64
-ALG_BYTES = {
-    "cgA_dir": lambda nu, npf, d: (3 * W_BYTES + 1) * nu,
-    "cgA_matvec": lambda nu, npf, d: (2 * W_BYTES + 1) * nu,
-    "cgA_update": lambda nu, npf, d: (6 * W_BYTES + 1) * nu,
-    "cgS_dir": lambda nu, npf, d: 4 * W_BYTES * npf,
-    "cgS_matvec": lambda nu, npf, d: (2 * W_BYTES + 1 + d) * npf,
-    "cgS_update": lambda nu, npf, d: 7 * W_BYTES * npf,
-}
+
+
+# Per hot kernel: algorithmic bytes and FP64/FP32 FLOPs for n_u unknown faces and n_p
+# fluid cells (w = 8 or 4 bytes; 4-byte work-list entry and 1 flag byte per unknown;
+# the SIMPLE stencil touches 2 n_u open faces, 3 FLOP each).
+def kernel_model(name, nu, npf, d):
+    w = 4 if name.endswith("_f32") else 8
+    base = name.replace("_f32", "")
+    bytes_ = {
+        "cgA_dir": (3 * w + 1 + 4) * nu,
+        "cgA_matvec": (2 * w + 1 + 4) * nu,
+        "cgA_update": (6 * w + 1 + 4) * nu,
+        "cgS_dir": (4 * w + 4) * npf,
+        "cgS_matvec": (2 * w + 4) * npf + 2 * nu,
+        "cgS_update": (7 * w + 4) * npf,
+    }[base]
+    flops = {
+        "cgA_dir": 3 * nu, "cgA_matvec": 9 * nu, "cgA_update": 9 * nu,
+        "cgS_dir": 3 * npf, "cgS_matvec": 6 * nu + 2 * npf, "cgS_update": 9 * npf,
+    }[base]
+    return bytes_, flops, w
 
 
 def make_mask(rank: int = 0):
@@ -53,14 +68,22 @@ def make_mask(rank: int = 0):
     return synth.sphere_packing(w["n"], w["r_min"], w["r_max"], w["porosity"], w["seed"] + rank)
 
 
+def _gen(spec):
+    """Pool worker: one seeded sphere packing (edge, r_min, r_max, porosity, seed)."""
+    sys.path.insert(0, ROOT)
+    from paper_2307_05266_gb300 import synth
+    n, r0, r1, phi, seed = spec
+    return synth.sphere_packing(n, r0, r1, phi, seed)
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
             pk = json.load(f)
-        return float(pk["hbm_gbs"]), "measured"
+        return float(pk["hbm_gbs"]), float(pk.get("sm_max_mhz", 2070.0)), "measured"
     except Exception:
-        return 6800.0, "fallback"
+        return 6800.0, 2070.0, "fallback"
 
 
 # ---------------------------------------------------------------------------------
@@ -80,8 +103,6 @@ def oracle_sample(n_inner: int = 10) -> dict:
     """Time the oracle on a bounded sample of the workload: assembly, n_inner inner A
     iterations and n_inner inner SIMPLE iterations; scale to two whole solves with the
     oracle's recorded iteration counts."""
-    import numpy as np
-
     from oracle import mac, stokes
     mask = make_mask(0)
     t0 = time.perf_counter()
@@ -126,8 +147,8 @@ def run_oracle_subprocess(threads: int = 1) -> dict:
 def sample_text(s: dict) -> str:
     return (f"128^3 spheres workload: oracle assembly ({s['t_assemble']:.2f} s) + 10 inner A "
             f"({s['t_inner_A'] * 1e3:.1f} ms/it) and 10 inner SIMPLE ({s['t_inner_S'] * 1e3:.1f} "
-            f"ms/it) FP64 CG iterations, scaled to 2 whole solves with the oracle's recorded "
-            f"iteration counts {s['counts']}")
+            f"ms/it) FP64 CG iterations on one core, scaled to 2 whole solves with the "
+            f"oracle's recorded iteration counts {s['counts']}")
 
 
 def reference_arm(args):
@@ -170,6 +191,7 @@ class ClockSampler:
     def __init__(self, index: str):
         self.index = index
         self.proc = None
+        self.out = ""
 
     def __enter__(self):
         try:
@@ -182,7 +204,6 @@ class ClockSampler:
         return self
 
     def __exit__(self, *exc):
-        self.out = ""
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -211,15 +232,68 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = (len(xs) - 1) * q
+    lo, hi = math.floor(k), math.ceil(k)
+    return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
+
+
+def batch_specs(n_geom=64, seed=2024):
+    """Batched workload: edges uniform in {32, 48, ..., 128}, porosity U[0.15, 0.5],
+    radii U[2, 8) (upper radius r_min + 4..6 capped at 8), packing seed = index."""
+    from paper_2307_05266_gb300.synth import SplitMix64
+    rng = SplitMix64(seed)
+    specs = []
+    for i in range(n_geom):
+        n = 32 + 16 * rng.next_int(0, 6)
+        phi = 0.15 + 0.35 * rng.next_double()
+        r0 = 2.0 + 2.0 * rng.next_double()
+        r1 = min(8.0, r0 + 2.0 + 2.0 * rng.next_double())
+        specs.append((n, r0, r1, phi, 1000 + i))
+    return specs
+
+
+def serve_specs(n_req, max_edge, seed=7):
+    """Serving workload: edges uniform in {48, 64, ..., max_edge}, porosity U[0.1, 0.5],
+    radii U[2, 8), flow axis uniform over x/y/z, Poisson arrivals (rate set later)."""
+    from paper_2307_05266_gb300.synth import SplitMix64
+    rng = SplitMix64(seed)
+    specs, axes = [], []
+    for i in range(n_req):
+        n = 48 + 16 * rng.next_int(0, (max_edge - 48) // 16)
+        phi = 0.10 + 0.40 * rng.next_double()
+        r0 = 2.0 + 2.0 * rng.next_double()
+        r1 = min(8.0, r0 + 2.0 + 2.0 * rng.next_double())
+        specs.append((n, r0, r1, phi, 5000 + i))
+        axes.append(rng.next_int(0, 2))
+    return specs, axes, rng
+
+
 def gpu_arm(args):
+    patterns = set() if args.patterns == "none" else set(args.patterns.split(","))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pool = pending = None
+    if world == 1 and (patterns & {"batch", "serve"}):
+        # masks of the extra patterns are generated by spawned workers (started before
+        # any GPU call) while the headline runs
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(min(8, os.cpu_count() or 1))
+        bspecs = batch_specs() if "batch" in patterns else []
+        sspecs, saxes, srng = serve_specs(args.serve_requests, args.serve_max_edge)
+        if "serve" not in patterns:
+            sspecs = []
+        pending = (pool.map_async(_gen, bspecs), pool.map_async(_gen, sspecs))
+
     import torch
     import torch.distributed as dist
 
     from paper_2307_05266_gb300 import binding
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -236,6 +310,7 @@ def gpu_arm(args):
     porosity = float(mask_np.mean())
     stream = torch.cuda.current_stream()
     precs = (("uzawa", binding.UZAWA), ("simple", binding.SIMPLE))
+    solve_kw = dict(tol=w["tol"], tol_inner_A=w["tol_inner"], tol_inner_S=w["tol_inner"])
 
     def step(mask, rec):
         g = binding.Geometry(mask)
@@ -243,8 +318,7 @@ def gpu_arm(args):
         launches = 2  # flags + S-hat diagonal
         for name, pc in precs:
             t0 = time.perf_counter()
-            st = g.solve(precond=pc, tol=w["tol"], tol_inner_A=w["tol_inner"],
-                         tol_inner_S=w["tol_inner"])
+            st = g.solve(precond=pc, **solve_kw)
             rs = g.recover_velocity()
             k = g.permeability(0)
             t1 = time.perf_counter()
@@ -297,12 +371,21 @@ def gpu_arm(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     e2e_value = solves / (float(t.item()) / 1e3)
 
+    per = {}
+    for name, rows in rec.items():
+        per[name] = {"ms_median": statistics.median(r["ms"] for r in rows),
+                     "outer": rows[-1]["outer"], "inner_A": rows[-1]["inner_A"],
+                     "inner_S": rows[-1]["inner_S"], "recovery": rows[-1]["recovery"],
+                     "k": rows[-1]["k"], "rel_res": rows[-1]["rel_res"]}
+
     # per-kernel timing: CUDA events around single launches on the bench stream, L2
-    # flushed (a 512 MiB write) before every launch
+    # flushed (a 512 MiB write) before every launch; FP32 kernels after a mixed solve
+    peak_bw, sm_mhz, peak_kind = load_peaks()
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    fp64_peak = nsm * 2 * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s: 2 DFMA/clk/SM, 2 FLOP each
     g = binding.Geometry(mask_dev)
     g.set_force(w["force"])
-    g.solve(precond=binding.SIMPLE, tol=w["tol"], tol_inner_A=w["tol_inner"],
-            tol_inner_S=w["tol_inner"])
+    g.solve(precond=binding.SIMPLE, precision=binding.MIXED, tol=w["tol"])
     info = g.info
     nu = int(sum(info.n_unknown[a] for a in range(info.ndim)))
     npf = int(info.n_fluid)
@@ -314,31 +397,41 @@ def gpu_arm(args):
             flush.zero_()
             times.append(g.time_kernel(name))
         avg = statistics.mean(times[2:])
-        alg = ALG_BYTES[name](nu, npf, info.ndim)
-        kern[name] = {"ms": avg, "alg_bytes": alg, "alg_GBps": alg / (avg / 1e3) / 1e9}
+        b, fl, wb = kernel_model(name, nu, npf, info.ndim)
+        gbps = b / (avg / 1e3) / 1e9
+        tflops = fl / (avg / 1e3) / 1e12
+        f_hbm, f_alu = gbps / peak_bw, (tflops / fp64_peak if wb == 8 else 0.0)
+        kern[name] = {"ms": avg, "alg_bytes": b, "alg_GBps": gbps, "fp64_flop": fl if wb == 8 else 0,
+                      "TFLOPs": tflops, "frac_hbm": f_hbm, "frac_fp64": f_alu,
+                      "bound": "alu" if f_alu > f_hbm else "hbm"}
     g.close()
-    peak, peak_kind = load_peaks()
-    # dominant kernel: largest share of one inner A iteration
-    dom = max(("cgA_dir", "cgA_matvec", "cgA_update"), key=lambda k: kern[k]["ms"])
-    roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["alg_GBps"], "peak": peak,
-            "unit": "GB/s", "frac": kern[dom]["alg_GBps"] / peak, "traffic": None,
-            "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind ==
-            "measured" else "fallback",
-            "timing": "CUDA events around single launches on the bench stream after the "
-                      "timed region, L2 flushed before each launch, mean of 10"}
+    del flush
+    # time share of each FP64 kernel in one headline step (launch counts from iterations)
+    launches_of = {"A": sum(per[p]["inner_A"] + per[p]["recovery"] for p in per),
+                   "S": sum(per[p]["inner_S"] for p in per)}
+    share = {k: kern[k]["ms"] * launches_of[k[2]] for k in
+             ("cgA_dir", "cgA_matvec", "cgA_update", "cgS_dir", "cgS_matvec", "cgS_update")}
+    tot = sum(share.values())
+    for k in share:
+        kern[k]["step_share"] = share[k] / tot
+    dom = max(share, key=share.get)
 
-    per = {}
-    for name, rows in rec.items():
-        per[name] = {"ms_median": statistics.median(r["ms"] for r in rows),
-                     "outer": rows[-1]["outer"], "inner_A": rows[-1]["inner_A"],
-                     "inner_S": rows[-1]["inner_S"], "recovery": rows[-1]["recovery"],
-                     "k": rows[-1]["k"], "rel_res": rows[-1]["rel_res"]}
+    def roof_of(name):
+        kk = kern[name]
+        if kk["bound"] == "alu":
+            return {"bound": "alu", "kernel": name, "achieved": kk["TFLOPs"], "peak": fp64_peak,
+                    "unit": "TFLOP/s", "frac": kk["frac_fp64"], "traffic": None,
+                    "peak_kind": f"derived FP64 peak: {nsm} SMs x 2 DFMA/clk x 2 FLOP x "
+                                 f"{sm_mhz:.0f} MHz"}
+        return {"bound": "hbm", "kernel": name, "achieved": kk["alg_GBps"], "peak": peak_bw,
+                "unit": "GB/s", "frac": kk["frac_hbm"], "traffic": None,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
 
-    if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
-        return 0
-    cpu = run_oracle_subprocess(1) if world == 1 else None
+    roof = roof_of(dom)
+    roof["timing"] = ("CUDA events around single launches on the bench stream after the timed "
+                      "region, L2 flushed before each launch, mean of 10; dominant kernel = "
+                      "largest time share of the headline step")
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -353,11 +446,29 @@ def gpu_arm(args):
         "per_precond": per,
         "kernels": kern,
         "roofline": roof,
+        "roofline_mixed": roof_of(max(("cgA_dir_f32", "cgA_matvec_f32", "cgA_update_f32",
+                                       "cgS_dir_f32", "cgS_matvec_f32", "cgS_update_f32"),
+                                      key=lambda k: kern[k]["ms"])),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(mask_np.nbytes),
                 "d2h_bytes_per_step": 16},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
+
+    if world == 1 and "mixed" in patterns:
+        line["mixed_precision"] = mixed_pattern(binding, mask_dev, per, solve_kw)
+    if pending is not None:
+        bmasks, smasks = pending[0].get(), pending[1].get()
+        pool.close()
+        if "batch" in patterns:
+            line["batched"] = batch_pattern(binding, torch, bmasks, stream)
+        if "serve" in patterns:
+            line["serving"] = serve_pattern(binding, torch, smasks, saxes, srng, args)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    cpu = run_oracle_subprocess(1) if world == 1 else None
     if cpu is not None and cpu.get("ok"):
         line["cpu_baseline"] = {"value": cpu["value"], "unit": UNIT, "cores": 1,
                                 "kind": "oracle", "sample": sample_text(cpu)}
@@ -370,12 +481,128 @@ def gpu_arm(args):
     return 0
 
 
+def mixed_pattern(binding, mask_dev, per, solve_kw):
+    """FP32 inner / FP64 outer solves of the headline workload, against the FP64 results."""
+    out = {}
+    counts = oracle_iteration_counts()
+    g = binding.Geometry(mask_dev)
+    g.set_force(WORKLOAD["force"])
+    for name, pc in (("uzawa", binding.UZAWA), ("simple", binding.SIMPLE)):
+        times = []
+        for i in range(3):
+            t0 = time.perf_counter()
+            st = g.solve(precond=pc, precision=binding.MIXED, tol=WORKLOAD["tol"],
+                         tol_inner_A=WORKLOAD["tol_inner"])
+            g.recover_velocity()
+            k = g.permeability(0)
+            if i:
+                times.append((time.perf_counter() - t0) * 1e3)
+        k64 = per[name]["k"]
+        ko = counts.get(name, {}).get("k", [None])[0]
+        out[name] = {"ms_median": statistics.median(times), "outer": st.outer_iters,
+                     "refinements": st.refinements, "inner_A_f32": st.inner_iters_A_f32,
+                     "inner_S_f32": st.inner_iters_S_f32, "inner_A_f64": st.inner_iters_A,
+                     "k": k, "k_rel_err_vs_gpu_fp64": abs(k - k64) / abs(k64),
+                     "k_rel_err_vs_oracle": (abs(k - ko) / abs(ko)) if ko else None,
+                     "speedup_vs_fp64": per[name]["ms_median"] / statistics.median(times)}
+    g.close()
+    return out
+
+
+def batch_pattern(binding, torch, masks, stream):
+    """64 uneven packings: one graph launch for all (autotuned launch shape) against the
+    same 64 solved one after another, mixed precision; FP64 sequential on the first 8."""
+    opts = dict(precond=binding.UZAWA, precision=binding.MIXED, tol=1e-8)
+    geoms = [binding.Geometry(torch.from_numpy(m).cuda()) for m in masks]
+    best, tune_ms = binding.Batch.autotune(geoms[:8], **opts)
+    b = binding.Batch(geoms, blocks_per_sm=best, **opts)
+    b.run()                                             # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ss, rs, ks = b.run()
+    t_batch = time.perf_counter() - t0
+    b.close()
+    t0 = time.perf_counter()
+    for g in geoms:
+        g.solve(**opts)
+        g.recover_velocity()
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for g in geoms[:8]:
+        g.solve(precond=binding.UZAWA, tol=1e-8)
+        g.recover_velocity()
+    t_seq64 = (time.perf_counter() - t0) / 8
+    cells = [m.size for m in masks]
+    for g in geoms:
+        g.close()
+    return {"n_geometries": len(masks), "edges": sorted({m.shape[0] for m in masks}),
+            "cells_total": int(sum(cells)), "precond": "uzawa", "precision": "mixed",
+            "autotuned_blocks_per_sm": best, "batch_s": t_batch,
+            "batch_solves_per_s": len(masks) / t_batch,
+            "sequential_mixed_solves_per_s": len(masks) / t_seq,
+            "sequential_fp64_solves_per_s_first8": 1.0 / t_seq64,
+            "speedup_batch_vs_sequential_mixed": t_seq / t_batch,
+            "all_converged": all(s.status == 0 for s in ss)}
+
+
+def serve_pattern(binding, torch, masks, axes, rng, args):
+    """Poisson-arrival serving at 80 % of the measured closed-loop capacity."""
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.6 * free)
+    # Uzawa needs thousands of outer iterations on the tightest requests (porosity ~0.1):
+    # the stagnation of Section 4.1 that motivates SIMPLE; the cap is raised accordingly
+    opts = dict(precond=binding.UZAWA, precision=binding.MIXED, tol=1e-8, max_outer=20000)
+
+    def run(arrivals, max_active):
+        srv = binding.Server(budget, max_active=max_active, **opts)
+        t0 = time.perf_counter()
+        sub = 0
+        res = {}
+        while len(res) < len(arrivals):
+            now = time.perf_counter() - t0
+            while sub < len(arrivals) and arrivals[sub] <= now:
+                srv.submit(masks[sub], axis=axes[sub])
+                sub += 1
+            srv.progress()
+            for r in srv.take():
+                res[r["id"]] = r
+            time.sleep(0.0002)
+        info = srv.info()
+        srv.close()
+        return [res[i + 1] for i in range(len(arrivals))], time.perf_counter() - t0, info
+
+    ncal = min(8, len(masks))
+    cal, t_cal, _ = run([0.0] * ncal, 8)
+    capacity = ncal / max(1e-9, max(r["t_done"] for r in cal))
+    rate = 0.8 * capacity
+    arrivals, t = [], 0.0
+    for _ in masks:
+        t += -math.log(1.0 - rng.next_double()) / rate
+        arrivals.append(t)
+    res, wall, info = run(arrivals, 16)
+    lat = [r["t_done"] - r["t_submit"] for r in res]
+    return {"requests": len(masks), "edges": [int(round(m.size ** (1 / 3))) for m in masks],
+            "precond": "uzawa", "precision": "mixed", "arrival_rate_per_s": rate,
+            "capacity_per_s": capacity, "p50_s": pct(lat, 0.5), "p99_s": pct(lat, 0.99),
+            "solves_per_s": len(res) / max(r["t_done"] for r in res),
+            "peak_active": info["peak_active"], "peak_bytes": info["peak_bytes"],
+            "budget_bytes": budget, "all_ok": all(r["status"] == 0 for r in res),
+            "status": [r["status"] for r in res], "outer_iters": [r["outer_iters"] for r in res],
+            "latency_s": lat}
+
+
+import numpy as np  # noqa: E402  (used by the patterns)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--patterns", default="mixed,batch,serve")
+    ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--serve-max-edge", type=int, default=192)
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample:
