@@ -66,8 +66,10 @@ void free_all(Handle& H) {
     H.graph_recover = H.graph_solo = nullptr;
     void* bufs[] = {H.mask, H.flags, H.invdS, H.ax, H.ar, H.ap, H.aq, H.sx, H.sr, H.sp,
                     H.sq, H.op, H.orr, H.od, H.oq, H.og, H.u, H.partials, H.dctl,
-                    H.cmp, H.cmean, H.small_start, H.small_cells, H.ulist, H.flist,
-                    H.axf, H.arf, H.apf, H.aqf, H.sxf, H.srf, H.spf, H.sqf, H.invdSf};
+                    H.cmpc, H.cmean, H.small_start, H.small_cells, H.ulist, H.flist,
+                    H.axf, H.arf, H.apf, H.aqf, H.sxf, H.srf, H.spf, H.sqf, H.invdSf,
+                    H.ufl, H.fmask, H.fbase, H.cmask, H.cbase, H.invdSc, H.stage,
+                    H.nbA, H.nbS, H.codeS, H.dSc};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (H.hctl) cudaFreeHost(H.hctl);
@@ -144,60 +146,98 @@ int build_components(Handle& H, const uint8_t* m) {
     for (int k = 0; k < ncomp; ++k)
         if (remap[k] < 0) remap[k] = next++;
     const int nsmall = ncomp - nbig;
+    // compact cell order: fluid cells in C order (the order of flist)
+    std::vector<uint32_t> fl;
+    std::vector<int> cmpc;
+    for (long long c = 0; c < n; ++c)
+        if (comp[c] >= 0) {
+            comp[c] = remap[comp[c]];
+            fl.push_back((uint32_t)c);
+            cmpc.push_back(comp[c]);
+        }
     std::vector<int> start((size_t)nsmall + 1, 0);
-    for (long long c = 0; c < n; ++c) {
-        if (comp[c] < 0) continue;
-        comp[c] = remap[comp[c]];
-        if (comp[c] >= nbig) start[comp[c] - nbig + 1]++;
-    }
+    for (int k : cmpc)
+        if (k >= nbig) start[k - nbig + 1]++;
     for (int j = 0; j < nsmall; ++j) start[j + 1] += start[j];
     std::vector<int> cells((size_t)std::max(start[nsmall], 1));
     std::vector<int> fill(start.begin(), start.end() - 1);
-    for (long long c = 0; c < n; ++c)
-        if (comp[c] >= nbig) cells[fill[comp[c] - nbig]++] = (int)c;
-    // compact work lists: unknown faces (both cells fluid) and fluid cells, ascending
-    std::vector<uint32_t> ul, fl;
+    for (size_t mi = 0; mi < cmpc.size(); ++mi)
+        if (cmpc[mi] >= nbig) cells[fill[cmpc[mi] - nbig]++] = (int)mi;
+    // compact face order (a, z, y, x) and the row bitmaps of faces and cells
+    const int W = (g.nx + 31) / 32;
+    const long long frows = (long long)g.d * g.nz * g.ny, crows = (long long)g.nz * g.ny;
+    std::vector<uint32_t> ul, fmask((size_t)(frows * W), 0u), fbase((size_t)(frows * W), 0u);
+    std::vector<uint32_t> cmask((size_t)(crows * W), 0u), cbase((size_t)(crows * W), 0u);
     for (int a = 0; a < g.d; ++a)
         for (int z = 0; z < g.nz; ++z)
-            for (int y = 0; y < g.ny; ++y)
+            for (int y = 0; y < g.ny; ++y) {
+                const long long row = ((long long)a * g.nz + z) * g.ny + y;
                 for (int x = 0; x < g.nx; ++x) {
+                    if ((x & 31) == 0) fbase[row * W + (x >> 5)] = (uint32_t)ul.size();
                     const long long c = ((long long)z * g.ny + y) * g.nx + x;
                     if (m[c] != 1) continue;
-                    if (a == 0) fl.push_back((uint32_t)c);
                     int lx = x - (a == 0), ly = y - (a == 1), lz = z - (a == 2);
                     if (lx < 0) { if (!g.per[0]) continue; lx += g.nx; }
                     if (ly < 0) { if (!g.per[1]) continue; ly += g.ny; }
                     if (lz < 0) { if (!g.per[2]) continue; lz += g.nz; }
                     const long long l = ((long long)lz * g.ny + ly) * g.nx + lx;
-                    if (m[l] == 1) ul.push_back((uint32_t)(a * g.stride + c));
+                    if (m[l] != 1) continue;
+                    fmask[row * W + (x >> 5)] |= 1u << (x & 31);
+                    ul.push_back((uint32_t)(a * g.stride + c));
                 }
+            }
+    {
+        uint32_t cnt = 0;
+        for (long long row = 0; row < crows; ++row)
+            for (int x = 0; x < g.nx; ++x) {
+                if ((x & 31) == 0) cbase[row * W + (x >> 5)] = cnt;
+                if (m[row * g.nx + x] == 1) {
+                    cmask[row * W + (x >> 5)] |= 1u << (x & 31);
+                    ++cnt;
+                }
+            }
+    }
     H.n_u = (long long)ul.size();
     H.n_p = (long long)fl.size();
+    H.W = W;
     if (ul.empty()) ul.push_back(0);
-    if (fl.empty()) fl.push_back(0);
+    if (fl.empty()) { fl.push_back(0); cmpc.push_back(0); }
     H.n_comp = ncomp;
     H.n_big = nbig;
     H.n_small = nsmall;
-    cudaError_t e = alloc(H, &H.cmp, (size_t)n);
-    if (e == cudaSuccess) e = alloc(H, &H.cmean, (size_t)std::max(ncomp, 1));
-    if (e == cudaSuccess) e = alloc(H, &H.small_start, start.size());
-    if (e == cudaSuccess) e = alloc(H, &H.small_cells, cells.size());
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(H.cmp, comp.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, H.stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(H.small_start, start.data(), start.size() * sizeof(int),
-                            cudaMemcpyHostToDevice, H.stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(H.small_cells, cells.data(), cells.size() * sizeof(int),
-                            cudaMemcpyHostToDevice, H.stream);
-    if (e == cudaSuccess) e = alloc(H, &H.ulist, ul.size());
-    if (e == cudaSuccess) e = alloc(H, &H.flist, fl.size());
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(H.ulist, ul.data(), ul.size() * sizeof(uint32_t),
-                            cudaMemcpyHostToDevice, H.stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(H.flist, fl.data(), fl.size() * sizeof(uint32_t),
-                            cudaMemcpyHostToDevice, H.stream);
+    const size_t nu = ul.size(), np = fl.size();
+    cudaError_t e = cudaSuccess;
+    auto up = [&](auto** dst, const auto& src) {
+        if (e == cudaSuccess) e = alloc(H, dst, src.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(src[0]), cudaMemcpyHostToDevice,
+                                H.stream);
+    };
+    up(&H.cmpc, cmpc);
+    up(&H.small_start, start);
+    up(&H.small_cells, cells);
+    up(&H.ulist, ul);
+    up(&H.flist, fl);
+    up(&H.fmask, fmask);
+    up(&H.fbase, fbase);
+    up(&H.cmask, cmask);
+    up(&H.cbase, cbase);
+    auto A = [&](auto** p, size_t cnt) { if (e == cudaSuccess) e = alloc(H, p, cnt); };
+    A(&H.cmean, (size_t)std::max(ncomp, 1));
+    A(&H.ufl, nu);
+    A(&H.invdSc, np);
+    A(&H.dSc, np);
+    // p vectors carry one more entry, kept at 0, that missing stencil neighbours point at
+    A(&H.ax, nu); A(&H.ar, nu); A(&H.ap, nu + 1); A(&H.aq, nu);
+    A(&H.sx, np); A(&H.sr, np); A(&H.sp, np + 1); A(&H.sq, np);
+    H.ldA = (long long)(nu + 31) / 32 * 32;
+    H.ldS = (long long)(np + 31) / 32 * 32;
+    A(&H.nbA, (size_t)(2 * g.d * H.ldA));
+    A(&H.nbS, (size_t)(2 * g.d * H.ldS));
+    A(&H.codeS, np);
+    if (e == cudaSuccess) e = launch_gather_u8(H, H.flags, H.ulist, H.ufl, (long long)nu);
+    if (e == cudaSuccess) e = launch_gather_f64(H, H.invdS, H.flist, H.invdSc, (long long)np);
+    if (e == cudaSuccess) e = launch_build_tables(H);
     if (e == cudaSuccess) e = cudaStreamSynchronize(H.stream);  // host vectors go out of scope
     if (e == cudaErrorMemoryAllocation) return set_error(SCHUR_ENOMEM, "device allocation failed");
     if (e != cudaSuccess) return cuda_error(e, "component upload");
@@ -284,12 +324,12 @@ int check_opts(const schur_opts& o) {
 int prepare_solve(Handle& H, const schur_opts& o, int use_graph) {
     if (o.precision == SCHUR_MIXED && !H.axf) {
         // FP32 inner-solve buffers, allocated on the first mixed-precision solve
-        const size_t nf = (size_t)H.g.d * H.g.stride, nc = (size_t)H.g.ncell;
+        const size_t nu = (size_t)std::max(H.n_u, 1ll), np = (size_t)std::max(H.n_p, 1ll);
         cudaError_t e = cudaSuccess;
         auto A = [&](float** p, size_t n) { if (e == cudaSuccess) e = alloc(H, p, n); };
-        A(&H.axf, nf); A(&H.arf, nf); A(&H.apf, nf); A(&H.aqf, nf);
-        A(&H.sxf, nc); A(&H.srf, nc); A(&H.spf, nc); A(&H.sqf, nc); A(&H.invdSf, nc);
-        if (e == cudaSuccess) e = launch_to_float(H, H.invdS, H.invdSf, (long long)nc);
+        A(&H.axf, nu); A(&H.arf, nu); A(&H.apf, nu + 1); A(&H.aqf, nu);
+        A(&H.sxf, np); A(&H.srf, np); A(&H.spf, np + 1); A(&H.sqf, np); A(&H.invdSf, np);
+        if (e == cudaSuccess) e = launch_to_float(H, H.invdSc, H.invdSf, (long long)np);
         if (e == cudaErrorMemoryAllocation) return set_error(SCHUR_ENOMEM, "device allocation failed");
         if (e != cudaSuccess) return cuda_error(e, "mixed-precision buffers");
     }
@@ -433,8 +473,6 @@ int schur_create_geometry(const uint8_t* mask, int ndim, const int64_t dims[3],
     A(&H.mask, nc);
     A(&H.flags, nf);
     A(&H.invdS, nc);
-    A(&H.ax, nf); A(&H.ar, nf); A(&H.ap, nf); A(&H.aq, nf);
-    A(&H.sx, nc); A(&H.sr, nc); A(&H.sp, nc); A(&H.sq, nc);
     A(&H.op, nc); A(&H.orr, nc); A(&H.od, nc); A(&H.oq, nc); A(&H.og, nc);
     A(&H.u, nf);
     A(&H.partials, (size_t)kMaxBlocks * 8);
@@ -705,18 +743,21 @@ int schur_solve_A(schur_geom_t G, const double* b, double* x, double tol, int ma
     reset_call(H, 1);
     c->solo.tol = tol;
     c->solo.max_iter = max_iter;
-    // the right-hand side is staged in aq (matvec output, rewritten before use)
-    CUDA_TRY(cudaMemcpyAsync(H.aq, b, nf * sizeof(double), cudaMemcpyDeviceToDevice, H.stream),
+    // the right-hand side is staged in a dense buffer of the handle (allocated on first use)
+    if (!H.stage) {
+        cudaError_t e = alloc(H, &H.stage, nf);
+        if (e == cudaErrorMemoryAllocation) return set_error(SCHUR_ENOMEM, "device allocation failed");
+        if (e != cudaSuccess) return cuda_error(e, "staging buffer");
+    }
+    CUDA_TRY(cudaMemcpyAsync(H.stage, b, nf * sizeof(double), cudaMemcpyDeviceToDevice, H.stream),
              "stage rhs");
     int rc = build_graph(H, &H.graph_solo, &H.exec_solo,
-                         [&](Recorder& R) { record_solve_A(H, R, H.aq, H.ax); });
+                         [&](Recorder& R) { record_solve_A(H, R, H.stage, H.ax); });
     if (rc) return rc;
     if ((rc = upload(H))) return rc;
     CUDA_TRY(cudaGraphLaunch(H.exec_solo, H.stream), "cudaGraphLaunch");
-    CUDA_TRY(cudaMemcpyAsync(x, H.ax, nf * sizeof(double), cudaMemcpyDeviceToDevice, H.stream),
-             "copy solution");
-    // the staging buffer held caller values off the unknowns: restore the zero invariant
-    CUDA_TRY(cudaMemsetAsync(H.aq, 0, nf * sizeof(double), H.stream), "clear staging");
+    CUDA_TRY(cudaMemsetAsync(x, 0, nf * sizeof(double), H.stream), "clear solution");
+    CUDA_TRY(launch_scatter_f64(H, H.ax, H.ulist, x, H.n_u), "scatter solution");
     if ((rc = download(H))) return rc;
     if (iters) *iters = c->solo.iter;
     const int st = map_status(c->solo.status);

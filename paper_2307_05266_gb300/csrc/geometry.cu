@@ -203,6 +203,37 @@ __global__ void k_to_float(const double* __restrict__ src, float* __restrict__ d
         dst[i] = (float)src[i];
 }
 
+__global__ void k_gather_u8(const uint8_t* __restrict__ src, const uint32_t* __restrict__ idx,
+                            uint8_t* __restrict__ dst, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[idx[i]];
+}
+__global__ void k_gather_f64(const double* __restrict__ src, const uint32_t* __restrict__ idx,
+                             double* __restrict__ dst, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[idx[i]];
+}
+__global__ void k_scatter_f64(const double* __restrict__ src, const uint32_t* __restrict__ idx,
+                              double* __restrict__ dst, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[idx[i]] = src[i];
+}
+cudaError_t launch_gather_u8(Handle& H, const uint8_t* src, const uint32_t* idx, uint8_t* dst, long long n) {
+    k_gather_u8<<<H.target_blocks, kBlock, 0, H.stream>>>(src, idx, dst, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_gather_f64(Handle& H, const double* src, const uint32_t* idx, double* dst, long long n) {
+    k_gather_f64<<<H.target_blocks, kBlock, 0, H.stream>>>(src, idx, dst, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_scatter_f64(Handle& H, const double* src, const uint32_t* idx, double* dst, long long n) {
+    k_scatter_f64<<<H.target_blocks, kBlock, 0, H.stream>>>(src, idx, dst, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_to_float(Handle& H, const double* src, float* dst, long long n) {
     k_to_float<<<H.target_blocks, kBlock, 0, H.stream>>>(src, dst, n);
     return cudaGetLastError();

@@ -33,14 +33,31 @@ struct Handle {
     float *axf = nullptr, *arf = nullptr, *apf = nullptr, *aqf = nullptr;
     float *sxf = nullptr, *srf = nullptr, *spf = nullptr, *sqf = nullptr, *invdSf = nullptr;
     // connected fluid components (connectivity through unknown faces)
-    int* cmp = nullptr;          // [ncell] component id, -1 on solid cells
+    int* cmpc = nullptr;         // [n_p] component id of each fluid cell (compact order)
     double* cmean = nullptr;     // [n_comp] per-component mean of the last projected vector
     int* small_start = nullptr;  // [n_small + 1] CSR offsets of the small components
-    int* small_cells = nullptr;  // cells of the small components, increasing per component
+    int* small_cells = nullptr;  // compact indices of the small components' cells
     int n_comp = 0, n_big = 0, n_small = 0;
-    // compact work lists (ascending): unknown faces (index into [d][stride]), fluid cells
-    uint32_t* ulist = nullptr;
-    uint32_t* flist = nullptr;
+    // compact layout of the inner solves: unknown faces in (a, z, y, x) order and fluid
+    // cells in (z, y, x) order; per row of nx positions a bitmap word and the compact
+    // index of the word's first set bit, so that a neighbour's compact index is a popcount
+    uint32_t* ulist = nullptr;   // [n_u] face index (into [d][stride]) of unknown k
+    uint32_t* flist = nullptr;   // [n_p] cell index of fluid cell m
+    uint8_t* ufl = nullptr;      // [n_u] flag byte of unknown k
+    uint32_t *fmask = nullptr, *fbase = nullptr;  // face rows: [d * nz * ny][W]
+    uint32_t *cmask = nullptr, *cbase = nullptr;  // cell rows: [nz * ny][W]
+    int W = 1;                   // 32-bit words per row
+    // neighbour tables of the stencils, built once per geometry from the bitmaps (row e
+    // of a table holds, for every entry, the compact index of its neighbour in direction
+    // e = 2 axis + (0: minus, 1: plus); a missing neighbour points at the entry one past
+    // the end of the vectors, which is kept at 0)
+    uint32_t* nbA = nullptr;     // [2d][ldA] neighbour faces of unknown k
+    uint32_t* nbS = nullptr;     // [2d][ldS] neighbour cells of fluid cell m across open faces
+    uint32_t* codeS = nullptr;   // [n_p] 3 bits per direction: 0 closed, 1 + ghost count open
+    double* dSc = nullptr;       // [n_p] diagonal of S-hat_simple, compact
+    long long ldA = 0, ldS = 0;
+    double* invdSc = nullptr;    // [n_p] inverse S-hat diagonal, compact
+    double* stage = nullptr;     // [d][stride] staging of schur_solve_A's right-hand side
     long long n_u = 0, n_p = 0;
     double* partials = nullptr;  // reduction scratch
     Ctl* dctl = nullptr;         // device control block
@@ -79,6 +96,12 @@ cudaError_t launch_apply_B(Handle& H, const double* u, double* p);
 cudaError_t launch_apply_BT(Handle& H, const double* p, double* u);
 cudaError_t launch_apply_simple(Handle& H, const double* p, double* q);
 cudaError_t launch_to_float(Handle& H, const double* src, float* dst, long long n);
+cudaError_t launch_gather_u8(Handle& H, const uint8_t* src, const uint32_t* idx, uint8_t* dst, long long n);
+cudaError_t launch_gather_f64(Handle& H, const double* src, const uint32_t* idx, double* dst, long long n);
+cudaError_t launch_scatter_f64(Handle& H, const double* src, const uint32_t* idx, double* dst, long long n);
+
+// krylov.cu: fill nbA, nbS, codeS and dSc from the row bitmaps and the face flags
+cudaError_t launch_build_tables(Handle& H);
 
 // krylov.cu: record the control flow of a call into R (graph nodes or direct launches)
 void record_solve(Handle& H, Recorder& R, int precond, int precision);

@@ -17,6 +17,12 @@
 // alpha = d.r / d.q) over FP32 inner solves, inside FP64 defect correction: each
 // refinement step runs FCG on S delta = r until ||r|| drops by a fixed factor, then
 // recomputes the true residual r = g - S p with FP64 inner solves.
+// Layout: the vectors of the inner solves are compact, one entry per unknown face (in
+// (a, z, y, x) order) or per fluid cell (in (z, y, x) order), so the streaming kernels
+// are dense, coalesced loops.  Stencil neighbours are found through per-row bitmaps: for
+// every row of nx positions, one 32-bit word per 32 positions and the compact index of
+// that word's first set bit; a neighbour's compact index is base + popcount.  The outer
+// vectors stay dense in cell space (0 on solid cells).
 // All scalars live in the device control block; every loop is a conditional while node
 // of one CUDA graph (or a host loop in debugging mode).  Every loop terminates: each
 // condition update either continues below its iteration cap or stops.
@@ -45,15 +51,6 @@ namespace schur {
          i += (long long)gridDim.x * blockDim.x)
 
 __device__ __forceinline__ bool is_thread0() { return threadIdx.x == 0 && threadIdx.y == 0; }
-
-template <typename T>
-__device__ __forceinline__ double face_val(const Dev& g, const uint8_t* __restrict__ flags,
-                                           const T* __restrict__ u, int a, int x, int y, int z) {
-    long long c = cell_at(g, x, y, z);
-    if (c < 0) return 0.0;
-    const long long i = (long long)a * g.stride + c;
-    return (flags[i] & 1) ? (double)u[i] : 0.0;
-}
 
 // per-type views of the ghost-count tables
 template <typename T> struct Tab;
@@ -115,13 +112,11 @@ __device__ __forceinline__ void finish_matvec(Ctl* ctl, CgState* st, double dq, 
 }
 
 // ------------------------------------------------------------------------------------
-// access patterns
+// access patterns and the compact layout
 // ------------------------------------------------------------------------------------
-// Streaming kernels walk compact work lists (unknown faces, fluid cells): a warp owns
-// kU chunks of 32 list entries per step (lane l takes entry base + l + 32 j), so each
-// thread has kU independent gathers in flight and every lane does useful work.  Faces
-// that are not unknowns and solid cells hold 0 in every solver vector from allocation
-// on and are never read or written.
+// Streaming kernels: a warp owns kU chunks of 32 consecutive compact entries per step
+// (lane l takes entry base + l + 32 j), every load is a coalesced row, and each thread
+// has kU independent loads in flight.
 constexpr int kU = 4;
 
 #define WARP_STREAM_BEGIN(n)                                                              \
@@ -137,26 +132,61 @@ constexpr int kU = 4;
         }               \
     }
 
-// Column tiles (used once per inner solve): x-y tiles strided over blockIdx.x,
-// gridDim.y = z chunks, blockIdx.z = component.
-#define COLUMN_TILES_BEGIN(g)                                                         \
-    const int gx_ = ((g).nx + kTileX - 1) / kTileX;                                   \
-    const int gy_ = ((g).ny + kTileY - 1) / kTileY;                                   \
-    const int zc_ = ((g).nz + gridDim.y - 1) / gridDim.y;                             \
-    const int z0_ = blockIdx.y * zc_;                                                 \
-    const int z1_ = min((g).nz, z0_ + zc_);                                           \
-    const long long plane = (long long)(g).nx * (g).ny;                               \
-    for (int t_ = blockIdx.x; t_ < gx_ * gy_; t_ += gridDim.x) {                      \
-        const int x = (t_ % gx_) * kTileX + (int)threadIdx.x;                         \
-        const int y = (t_ / gx_) * kTileY + (int)threadIdx.y;                         \
-        if (x < (g).nx && y < (g).ny) {                                               \
-            const long long cxy = (long long)y * (g).nx + x;                          \
-            for (int z = z0_; z < z1_; ++z) {                                         \
-                const long long c = z * plane + cxy;
-#define COLUMN_TILES_END \
-            }            \
-        }                \
-    }
+// Row bitmaps of the compact layout.
+struct Compact {
+    const uint32_t* ulist;   // [n_u] face index of unknown k
+    const uint32_t* flist;   // [n_p] cell index of fluid cell m
+    const uint8_t* ufl;      // [n_u] flag byte of unknown k
+    const uint32_t* fmask;   // face rows (a, z, y): [d * nz * ny][W]
+    const uint32_t* fbase;
+    const uint32_t* cmask;   // cell rows (z, y): [nz * ny][W]
+    const uint32_t* cbase;
+    int W;
+    long long n_u, n_p;
+    const uint32_t* nbA;     // [2d][ldA] stencil neighbours of the unknown faces
+    const uint32_t* nbS;     // [2d][ldS] neighbours of the fluid cells across open faces
+    const uint32_t* codeS;   // [n_p] per direction 3 bits: 0 closed, 1 + ghost count
+    long long ldA, ldS;
+};
+
+__device__ __forceinline__ bool wrap3(const Dev& g, int& x, int& y, int& z) {
+    if (x < 0) { if (!g.per[0]) return false; x += g.nx; } else if (x >= g.nx) { if (!g.per[0]) return false; x -= g.nx; }
+    if (y < 0) { if (!g.per[1]) return false; y += g.ny; } else if (y >= g.ny) { if (!g.per[1]) return false; y -= g.ny; }
+    if (z < 0) { if (!g.per[2]) return false; z += g.nz; } else if (z >= g.nz) { if (!g.per[2]) return false; z -= g.nz; }
+    return true;
+}
+
+// Compact index of the entry at position x of a row, or -1 when the bit is clear.
+__device__ __forceinline__ long long row_rank(const uint32_t* __restrict__ mask,
+                                              const uint32_t* __restrict__ base, long long row,
+                                              int W, int x) {
+    const long long wi = row * W + (x >> 5);
+    const uint32_t m = mask[wi];
+    const uint32_t bit = 1u << (x & 31);
+    if (!(m & bit)) return -1;
+    return (long long)base[wi] + __popc(m & (bit - 1u));
+}
+
+// Compact index of face (a, x, y, z) (wrapped; -1 outside a closed box or not unknown).
+__device__ __forceinline__ long long face_rank(const Dev& g, const Compact& C, int a, int x,
+                                               int y, int z) {
+    if (!wrap3(g, x, y, z)) return -1;
+    return row_rank(C.fmask, C.fbase, ((long long)a * g.nz + z) * g.ny + y, C.W, x);
+}
+
+// Compact index of fluid cell (x, y, z) (wrapped; -1 outside or solid).
+__device__ __forceinline__ long long cell_rank(const Dev& g, const Compact& C, int x, int y, int z) {
+    if (!wrap3(g, x, y, z)) return -1;
+    return row_rank(C.cmask, C.cbase, (long long)z * g.ny + y, C.W, x);
+}
+
+// Value of a compact face vector at face (a, x, y, z), 0 when the face is not an unknown.
+template <typename T>
+__device__ __forceinline__ double face_valc(const Dev& g, const Compact& C, const T* __restrict__ u,
+                                            int a, int x, int y, int z) {
+    const long long k = face_rank(g, C, a, x, y, z);
+    return k < 0 ? 0.0 : (double)u[k];
+}
 
 // Decode a face index of [d][stride] (or a cell index) into component and coordinates.
 struct FaceAt {
@@ -177,139 +207,200 @@ __device__ __forceinline__ FaceAt decode_face(const Dev& g, uint32_t i) {
     return r;
 }
 
+// Neighbour tables, one thread per entry: the rank lookups of the row bitmaps run once
+// per geometry instead of once per stencil application.
+__global__ void k_build_nbA(Dev g, Compact C, uint32_t* __restrict__ nbA) {
+    STREAM_LOOP(k, C.n_u) {
+        const FaceAt f = decode_face(g, C.ulist[k]);
+        for (int e = 0; e < 2 * g.d; ++e) {
+            const int b = e >> 1, sgn = (e & 1) ? 1 : -1;
+            const long long r = face_rank(g, C, f.a, f.x + (b == 0) * sgn, f.y + (b == 1) * sgn,
+                                          f.z + (b == 2) * sgn);
+            nbA[e * C.ldA + k] = r < 0 ? (uint32_t)C.n_u : (uint32_t)r;
+        }
+    }
+}
+
+// Direction e = 2a is the lower face (a, c), e = 2a + 1 the upper face (a, c + e_a); an
+// open (unknown) face links the cell to the fluid cell on its other side.  dS is the
+// diagonal of S-hat_simple, the sum of the open faces' weights.
+__global__ void k_build_nbS(Dev g, Compact C, const uint8_t* __restrict__ flags,
+                            uint32_t* __restrict__ nbS, uint32_t* __restrict__ codeS,
+                            double* __restrict__ dS) {
+    STREAM_LOOP(m, C.n_p) {
+        const FaceAt f = decode_face(g, C.flist[m]);
+        uint32_t code = 0;
+        double diag = 0.0;
+        for (int e = 0; e < 2 * g.d; ++e) {
+            const int a = e >> 1, up = e & 1;
+            const int ex = a == 0, ey = a == 1, ez = a == 2;
+            uint32_t nb = (uint32_t)C.n_p;
+            int fx = f.x + up * ex, fy = f.y + up * ey, fz = f.z + up * ez;   // face position
+            if (wrap3(g, fx, fy, fz)) {
+                const uint8_t fl = flags[(long long)a * g.stride + ((long long)fz * g.ny + fy) * g.nx + fx];
+                if (fl & 1) {
+                    // the cell across the face: c - e_a (lower face) or c + e_a (upper face)
+                    const long long r = up ? cell_rank(g, C, fx, fy, fz)
+                                           : cell_rank(g, C, f.x - ex, f.y - ey, f.z - ez);
+                    if (r >= 0) {
+                        nb = (uint32_t)r;
+                        const int gh = (fl >> 1) & 7;
+                        code |= (uint32_t)(1 + gh) << (3 * e);
+                        diag += tab5(g.wdiag, gh);
+                    }
+                }
+            }
+            nbS[e * C.ldS + m] = nb;
+        }
+        codeS[m] = code;
+        dS[m] = diag;
+    }
+}
+
 // ------------------------------------------------------------------------------------
-// inner CG on A (face space)
+// inner CG on A (compact face space)
 // ------------------------------------------------------------------------------------
 // The inner A solve works with the dimensionless operator A' = h^2 A (diagonal 2d + g,
 // off-diagonal -1) and M' = diag(A'), right-hand side h^2 b: alpha, beta and every
 // iterate x are those of CG on A x = b with Jacobi M = diag(A), without h^-2 factors.
 
-// b = cf f_a + cp h^-1 (P_c - P_(c-e_a)) (+ bvec) on unknown faces (formed in FP64);
-// x = 0, r = h^2 b.
+// b = cf f_a + cp h^-1 (P_c - P_(c-e_a)) (+ bvec, dense face layout) on the unknowns
+// (formed in FP64); x = 0, r = h^2 b.  P is a dense cell vector.
 template <typename T>
-__global__ void k_cgA_init(Dev g, const uint8_t* __restrict__ flags, T* __restrict__ xv,
-                           T* __restrict__ rv, const double* __restrict__ P, double cp,
-                           double cf, const double* __restrict__ bvec, Ctl* ctl, CgState* st,
+__global__ void k_cgA_init(Dev g, Compact C, T* __restrict__ xv, T* __restrict__ rv,
+                           const double* __restrict__ P, double cp, double cf,
+                           const double* __restrict__ bvec, Ctl* ctl, CgState* st,
                            double* partials, int slot) {
     count_launch(ctl);
     double v[2] = {0.0, 0.0};
-    const int a = blockIdx.z;
-    const uint8_t* F = flags + (long long)a * g.stride;
-    const long long lower = a == 0 ? 1 : (a == 1 ? g.nx : (long long)g.nx * g.ny);
-    const double fa = cf * ctl->f[a];
-    COLUMN_TILES_BEGIN(g)
-        const uint8_t f = F[c];
-        if (f & 1) {
+    const long long plane = (long long)g.nx * g.ny;
+    STREAM_LOOP(k, C.n_u) {
+        const uint32_t i = C.ulist[k];
+        const FaceAt f = decode_face(g, i);
+        const int a = f.a;
+        double b = cf * ctl->f[a];
+        if (P) {
             // an unknown face has a fluid lower cell inside the box (wrap when periodic)
-            long long cl = c - lower;
-            if ((a == 0 && x == 0) || (a == 1 && y == 0) || (a == 2 && z == 0))
-                cl += (a == 0 ? g.nx : (a == 1 ? (long long)g.ny * g.nx : (long long)g.nz * plane));
-            double b = fa;
-            if (P) b += cp * (g.hinv * (P[c] - P[cl]));
-            const long long i = (long long)a * g.stride + c;
-            if (bvec) b += bvec[i];
-            const T bt = (T)(b * g.h2);  // right-hand side of h^2 A x = h^2 b
-            const double bd = (double)bt;
-            const double zz = bd * tab5(g.wdiag, f >> 1);
-            v[0] += bd * zz;
-            v[1] += zz * zz;
-            xv[i] = (T)0;
-            rv[i] = bt;
+            long long cl;
+            if (a == 0) cl = f.x > 0 ? f.c - 1 : f.c + g.nx - 1;
+            else if (a == 1) cl = f.y > 0 ? f.c - g.nx : f.c + (long long)(g.ny - 1) * g.nx;
+            else cl = f.z > 0 ? f.c - plane : f.c + (long long)(g.nz - 1) * plane;
+            b += cp * (g.hinv * (P[f.c] - P[cl]));
         }
-    COLUMN_TILES_END
+        if (bvec) b += bvec[i];
+        const T bt = (T)(b * g.h2);  // right-hand side of h^2 A x = h^2 b
+        const double bd = (double)bt;
+        const double zz = bd * tab5(g.wdiag, C.ufl[k] >> 1);
+        v[0] += bd * zz;
+        v[1] += zz * zz;
+        xv[k] = (T)0;
+        rv[k] = bt;
+    }
     if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0())
         set_cond(ctl, slot, start_inner(ctl, st, v[0], v[1]));
 }
 
-// p = M'^-1 r + beta p over the unknown-face list.
+// p = M'^-1 r + beta p.
 template <typename T>
-__global__ void k_cgA_dir(Dev g, const uint32_t* __restrict__ list, long long n,
-                          const uint8_t* __restrict__ flags, const T* __restrict__ rv,
-                          T* __restrict__ pv, Ctl* ctl, const CgState* st) {
+__global__ void k_cgA_dir(Dev g, long long n, const uint8_t* __restrict__ ufl,
+                          const T* __restrict__ rv, T* __restrict__ pv, Ctl* ctl,
+                          const CgState* st) {
     count_launch(ctl);
     const T beta = (T)(st->first ? 0.0 : st->beta);
     WARP_STREAM_BEGIN(n)
-        uint32_t i[kU];
         int gh[kU];
         T r[kU], p[kU];
 #pragma unroll
-        for (int j = 0; j < kU; ++j) i[j] = idx[j] < n ? list[idx[j]] : 0u;
+        for (int j = 0; j < kU; ++j)
+            if (idx[j] < n) { gh[j] = ufl[idx[j]] >> 1; r[j] = rv[idx[j]]; p[j] = pv[idx[j]]; }
 #pragma unroll
         for (int j = 0; j < kU; ++j)
-            if (idx[j] < n) { gh[j] = flags[i[j]] >> 1; r[j] = rv[i[j]]; p[j] = pv[i[j]]; }
-#pragma unroll
-        for (int j = 0; j < kU; ++j)
-            if (idx[j] < n) pv[i[j]] = r[j] * Tab<T>::w(g, gh[j]) + beta * p[j];
+            if (idx[j] < n) pv[idx[j]] = r[j] * Tab<T>::w(g, gh[j]) + beta * p[j];
     WARP_STREAM_END
 }
 
-// q = A' p and p.q over the unknown-face list; neighbours that are not unknowns hold 0.
+// Entries per thread and step of the stencil kernels (independent gathers in flight).
+template <typename T> struct MvU { static constexpr int v = 4; };
+template <> struct MvU<double> { static constexpr int v = 2; };
+
+#define WARP_STREAM_BEGIN_U(n, U)                                                         \
+    {                                                                                     \
+        const long long lane_ = threadIdx.x & 31;                                         \
+        const long long nw_ = ((long long)gridDim.x * blockDim.x) >> 5;                   \
+        for (long long base_ = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5)  \
+                               * (32 * (U));                                              \
+             base_ < (n); base_ += nw_ * (32 * (U))) {                                    \
+            long long idx[U];                                                             \
+            _Pragma("unroll") for (int j = 0; j < (U); ++j) idx[j] = base_ + lane_ + 32 * j;
+
+// q = A' p and p.q.  The neighbour indices come from the table (coalesced rows); missing
+// neighbours point at the zero entry p[n_u].
 template <typename T>
-__global__ void k_cgA_matvec(Dev g, const uint32_t* __restrict__ list, long long n,
-                             const uint8_t* __restrict__ flags, const T* __restrict__ pv,
-                             T* __restrict__ qv, Ctl* ctl, CgState* st, double* partials,
-                             int slot) {
+__global__ void __launch_bounds__(kBlock) k_cgA_matvec(Dev g, Compact C, const T* __restrict__ pv,
+                                                       T* __restrict__ qv, Ctl* ctl, CgState* st,
+                                                       double* partials, int slot) {
     count_launch(ctl);
     T acc = (T)0;
-    const long long plane = (long long)g.nx * g.ny;
-    STREAM_LOOP(k, n) {
-        const uint32_t i = list[k];
-        const FaceAt f = decode_face(g, i);
-        const int gh = flags[i] >> 1;
-        const T* P = pv + (long long)f.a * g.stride;
-        const long long c = f.c;
-        const T pc = P[c];
-        const long long xm = f.x > 0 ? c - 1 : (g.per[0] ? c + g.nx - 1 : -1);
-        const long long xp = f.x < g.nx - 1 ? c + 1 : (g.per[0] ? c - (g.nx - 1) : -1);
-        const long long ym = f.y > 0 ? c - g.nx : (g.per[1] ? c + (long long)(g.ny - 1) * g.nx : -1);
-        const long long yp = f.y < g.ny - 1 ? c + g.nx : (g.per[1] ? c - (long long)(g.ny - 1) * g.nx : -1);
-        T s = (xm >= 0 ? P[xm] : (T)0) + (xp >= 0 ? P[xp] : (T)0);
-        s += (ym >= 0 ? P[ym] : (T)0) + (yp >= 0 ? P[yp] : (T)0);
-        if (g.d == 3) {
-            const long long zm = f.z > 0 ? c - plane : (g.per[2] ? c + (long long)(g.nz - 1) * plane : -1);
-            const long long zp = f.z < g.nz - 1 ? c + plane : (g.per[2] ? c - (long long)(g.nz - 1) * plane : -1);
-            s += (zm >= 0 ? P[zm] : (T)0) + (zp >= 0 ? P[zp] : (T)0);
-        }
-        const T out = Tab<T>::diag(g, gh) * pc - s;
-        qv[i] = out;
-        acc += pc * out;
-    }
+    const long long n = C.n_u;
+    const int ne = 2 * g.d;
+    constexpr int U = MvU<T>::v;
+    WARP_STREAM_BEGIN_U(n, U)
+        uint32_t nb[U][6];
+        int gh[U];
+        T pc[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j)
+            if (idx[j] < n) {
+#pragma unroll
+                for (int e = 0; e < 6; ++e)
+                    nb[j][e] = e < ne ? __ldcs(C.nbA + e * C.ldA + idx[j]) : (uint32_t)n;
+                gh[j] = C.ufl[idx[j]] >> 1;
+                pc[j] = pv[idx[j]];
+            }
+#pragma unroll
+        for (int j = 0; j < U; ++j)
+            if (idx[j] < n) {
+                T sv[6];
+#pragma unroll
+                for (int e = 0; e < 6; ++e) sv[e] = pv[nb[j][e]];
+                const T s = ((sv[0] + sv[1]) + (sv[2] + sv[3])) + (sv[4] + sv[5]);
+                const T out = Tab<T>::diag(g, gh[j]) * pc[j] - s;
+                qv[idx[j]] = out;
+                acc += pc[j] * out;
+            }
+    WARP_STREAM_END
     double v[1] = {(double)acc};
     if (reduce_last_block<1>(v, partials, &ctl->ticket) && is_thread0())
         finish_matvec(ctl, st, v[0], slot);
 }
 
-// x += alpha p, r -= alpha q; r.z and z.z (z = M'^-1 r) over the unknown-face list.
+// x += alpha p, r -= alpha q; r.z and z.z (z = M'^-1 r).
 template <typename T>
-__global__ void k_cgA_update(Dev g, const uint32_t* __restrict__ list, long long n,
-                             const uint8_t* __restrict__ flags, T* __restrict__ xv,
-                             T* __restrict__ rv, const T* __restrict__ pv,
+__global__ void k_cgA_update(Dev g, long long n, const uint8_t* __restrict__ ufl,
+                             T* __restrict__ xv, T* __restrict__ rv, const T* __restrict__ pv,
                              const T* __restrict__ qv, Ctl* ctl, CgState* st,
                              double* partials, int slot) {
     count_launch(ctl);
     const T alpha = (T)st->alpha;
     T a0 = (T)0, a1 = (T)0;
     WARP_STREAM_BEGIN(n)
-        uint32_t i[kU];
         int gh[kU];
         T xx[kU], p[kU], r[kU], q[kU];
 #pragma unroll
-        for (int j = 0; j < kU; ++j) i[j] = idx[j] < n ? list[idx[j]] : 0u;
-#pragma unroll
         for (int j = 0; j < kU; ++j)
             if (idx[j] < n) {
-                gh[j] = flags[i[j]] >> 1;
-                xx[j] = xv[i[j]];
-                p[j] = pv[i[j]];
-                r[j] = rv[i[j]];
-                q[j] = qv[i[j]];
+                gh[j] = ufl[idx[j]] >> 1;
+                xx[j] = xv[idx[j]];
+                p[j] = pv[idx[j]];
+                r[j] = rv[idx[j]];
+                q[j] = qv[idx[j]];
             }
 #pragma unroll
         for (int j = 0; j < kU; ++j)
             if (idx[j] < n) {
-                xv[i[j]] = xx[j] + alpha * p[j];
+                xv[idx[j]] = xx[j] + alpha * p[j];
                 const T rn = r[j] - alpha * q[j];
-                rv[i[j]] = rn;
+                rv[idx[j]] = rn;
                 const T zz = rn * Tab<T>::w(g, gh[j]);
                 a0 += rn * zz;
                 a1 += zz * zz;
@@ -321,13 +412,13 @@ __global__ void k_cgA_update(Dev g, const uint32_t* __restrict__ list, long long
 }
 
 // ------------------------------------------------------------------------------------
-// inner CG on S-hat_simple (cell space); M^-1 = invd (0 on solid and isolated cells)
+// inner CG on S-hat_simple (compact cell space); M^-1 = invd (0 on isolated cells)
 // ------------------------------------------------------------------------------------
 
-// b = r - (its mean on r's fluid component): the FP64 outer residual r is projected onto
-// the range of S-hat in place, then x = 0 and the CG residual starts at b.
+// b = r - (its mean on r's fluid component): the dense FP64 outer residual r is projected
+// onto the range of S-hat in place, then x = 0 and the CG residual starts at b.
 template <typename T>
-__global__ void k_cgS_init(Dev g, const T* __restrict__ invd, const int* __restrict__ cmp,
+__global__ void k_cgS_init(Dev g, Compact C, const T* __restrict__ invd, const int* __restrict__ cmpc,
                            const double* __restrict__ cmean, double* __restrict__ b,
                            T* __restrict__ xv, T* __restrict__ rv, Ctl* ctl, CgState* st,
                            const CgState* outer, double* partials, int slot) {
@@ -337,89 +428,98 @@ __global__ void k_cgS_init(Dev g, const T* __restrict__ invd, const int* __restr
         return;
     }
     double v[2] = {0.0, 0.0};
-    STREAM_LOOP(c, g.ncell) {
-        const int k = cmp[c];
-        if (k >= 0) {
-            const double bc = b[c] - cmean[k];
-            b[c] = bc;
-            const T bt = (T)bc;
-            const double zz = (double)bt * (double)invd[c];
-            v[0] += (double)bt * zz;
-            v[1] += zz * zz;
-            xv[c] = (T)0;
-            rv[c] = bt;
-        }
+    STREAM_LOOP(m, C.n_p) {
+        const uint32_t c = C.flist[m];
+        const double bc = b[c] - cmean[cmpc[m]];
+        b[c] = bc;
+        const T bt = (T)bc;
+        const double zz = (double)bt * (double)invd[m];
+        v[0] += (double)bt * zz;
+        v[1] += zz * zz;
+        xv[m] = (T)0;
+        rv[m] = bt;
     }
     if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0())
         set_cond(ctl, slot, start_inner(ctl, st, v[0], v[1]));
 }
 
 template <typename T>
-__global__ void k_cgS_dir(Dev g, const uint32_t* __restrict__ list, long long n,
-                          const T* __restrict__ invd, const T* __restrict__ rv,
+__global__ void k_cgS_dir(Dev g, long long n, const T* __restrict__ invd, const T* __restrict__ rv,
                           T* __restrict__ pv, Ctl* ctl, const CgState* st) {
     count_launch(ctl);
     const T beta = (T)(st->first ? 0.0 : st->beta);
     WARP_STREAM_BEGIN(n)
-        uint32_t i[kU];
         T r[kU], w[kU], p[kU];
 #pragma unroll
-        for (int j = 0; j < kU; ++j) i[j] = idx[j] < n ? list[idx[j]] : 0u;
+        for (int j = 0; j < kU; ++j)
+            if (idx[j] < n) { r[j] = rv[idx[j]]; w[j] = invd[idx[j]]; p[j] = pv[idx[j]]; }
 #pragma unroll
         for (int j = 0; j < kU; ++j)
-            if (idx[j] < n) { r[j] = rv[i[j]]; w[j] = invd[i[j]]; p[j] = pv[i[j]]; }
-#pragma unroll
-        for (int j = 0; j < kU; ++j)
-            if (idx[j] < n) pv[i[j]] = r[j] * w[j] + beta * p[j];
+            if (idx[j] < n) pv[idx[j]] = r[j] * w[j] + beta * p[j];
     WARP_STREAM_END
 }
 
-// q = S-hat p and p.q over the fluid-cell list: the sum over the open faces of
-// (p_c - p_nb) / (2d + g_f).
+// Weight 1 / (2d + g) of an open face from its 3-bit code (0: closed face, weight 0).
 template <typename T>
-__global__ void k_cgS_matvec(Dev g, const uint32_t* __restrict__ list, long long n,
-                             const uint8_t* __restrict__ flags, const T* __restrict__ pv,
-                             T* __restrict__ qv, Ctl* ctl, CgState* st, double* partials,
-                             int slot) {
+__device__ __forceinline__ T face_weight(const Dev& g, uint32_t code) {
+    return code == 0u ? (T)0 : Tab<T>::w(g, (int)code - 1);
+}
+
+// q = S-hat p and p.q.  FP64 (bound by the FP64 pipe) forms diag(S-hat) p_c minus the
+// weighted neighbour sum; FP32 sums the weighted differences (p_c - p_nb), which vanish
+// exactly on constants.  Closed faces point at the zero entry p[n_p] with weight 0.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cgS_matvec(Dev g, Compact C, const T* __restrict__ dS,
+                                                       const T* __restrict__ pv, T* __restrict__ qv,
+                                                       Ctl* ctl, CgState* st, double* partials,
+                                                       int slot) {
     count_launch(ctl);
     T acc = (T)0;
-    const long long plane = (long long)g.nx * g.ny;
-    const uint8_t* F0 = flags;
-    const uint8_t* F1 = flags + g.stride;
-    const uint8_t* F2 = flags + 2 * g.stride;
-    STREAM_LOOP(k, n) {
-        const uint32_t ci = list[k];
-        const FaceAt f = decode_face(g, ci);
-        const long long c = f.c;
-        const T pc = pv[c];
-        T out = (T)0;
-        // lower faces: an unknown lower face has its lower cell inside the box
-        uint8_t fl = F0[c];
-        if (fl & 1) out += (pc - pv[f.x > 0 ? c - 1 : c + g.nx - 1]) * Tab<T>::w(g, fl >> 1);
-        fl = F1[c];
-        if (fl & 1) out += (pc - pv[f.y > 0 ? c - g.nx : c + (long long)(g.ny - 1) * g.nx]) * Tab<T>::w(g, fl >> 1);
-        // upper faces
-        const long long xp = f.x < g.nx - 1 ? c + 1 : (g.per[0] ? c - (g.nx - 1) : -1);
-        if (xp >= 0) { fl = F0[xp]; if (fl & 1) out += (pc - pv[xp]) * Tab<T>::w(g, fl >> 1); }
-        const long long yp = f.y < g.ny - 1 ? c + g.nx : (g.per[1] ? c - (long long)(g.ny - 1) * g.nx : -1);
-        if (yp >= 0) { fl = F1[yp]; if (fl & 1) out += (pc - pv[yp]) * Tab<T>::w(g, fl >> 1); }
-        if (g.d == 3) {
-            fl = F2[c];
-            if (fl & 1) out += (pc - pv[f.z > 0 ? c - plane : c + (long long)(g.nz - 1) * plane]) * Tab<T>::w(g, fl >> 1);
-            const long long zp = f.z < g.nz - 1 ? c + plane : (g.per[2] ? c - (long long)(g.nz - 1) * plane : -1);
-            if (zp >= 0) { fl = F2[zp]; if (fl & 1) out += (pc - pv[zp]) * Tab<T>::w(g, fl >> 1); }
-        }
-        qv[c] = out;
-        acc += pc * out;
-    }
+    const long long n = C.n_p;
+    const int ne = 2 * g.d;
+    constexpr int U = MvU<T>::v;
+    WARP_STREAM_BEGIN_U(n, U)
+        uint32_t nb[U][6], code[U];
+        T pc[U], dg[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j)
+            if (idx[j] < n) {
+#pragma unroll
+                for (int e = 0; e < 6; ++e)
+                    nb[j][e] = e < ne ? __ldcs(C.nbS + e * C.ldS + idx[j]) : (uint32_t)n;
+                code[j] = __ldcs(C.codeS + idx[j]);
+                pc[j] = pv[idx[j]];
+                if constexpr (sizeof(T) == 8) dg[j] = dS[idx[j]];
+            }
+#pragma unroll
+        for (int j = 0; j < U; ++j)
+            if (idx[j] < n) {
+                T sv[6];
+#pragma unroll
+                for (int e = 0; e < 6; ++e) sv[e] = pv[nb[j][e]];
+                T out;
+                if constexpr (sizeof(T) == 8) {
+                    T s = face_weight<T>(g, code[j] & 7u) * sv[0];
+#pragma unroll
+                    for (int e = 1; e < 6; ++e) s += face_weight<T>(g, (code[j] >> (3 * e)) & 7u) * sv[e];
+                    out = dg[j] * pc[j] - s;
+                } else {
+                    out = (T)0;
+#pragma unroll
+                    for (int e = 0; e < 6; ++e)
+                        out += face_weight<T>(g, (code[j] >> (3 * e)) & 7u) * (pc[j] - sv[e]);
+                }
+                qv[idx[j]] = out;
+                acc += pc[j] * out;
+            }
+    WARP_STREAM_END
     double v[1] = {(double)acc};
     if (reduce_last_block<1>(v, partials, &ctl->ticket) && is_thread0())
         finish_matvec(ctl, st, v[0], slot);
 }
 
 template <typename T>
-__global__ void k_cgS_update(Dev g, const uint32_t* __restrict__ list, long long n,
-                             const T* __restrict__ invd, T* __restrict__ xv,
+__global__ void k_cgS_update(Dev g, long long n, const T* __restrict__ invd, T* __restrict__ xv,
                              T* __restrict__ rv, const T* __restrict__ pv,
                              const T* __restrict__ qv, Ctl* ctl, CgState* st,
                              double* partials, int slot) {
@@ -427,25 +527,22 @@ __global__ void k_cgS_update(Dev g, const uint32_t* __restrict__ list, long long
     const T alpha = (T)st->alpha;
     T a0 = (T)0, a1 = (T)0;
     WARP_STREAM_BEGIN(n)
-        uint32_t i[kU];
         T xx[kU], p[kU], r[kU], q[kU], w[kU];
-#pragma unroll
-        for (int j = 0; j < kU; ++j) i[j] = idx[j] < n ? list[idx[j]] : 0u;
 #pragma unroll
         for (int j = 0; j < kU; ++j)
             if (idx[j] < n) {
-                xx[j] = xv[i[j]];
-                p[j] = pv[i[j]];
-                r[j] = rv[i[j]];
-                q[j] = qv[i[j]];
-                w[j] = invd[i[j]];
+                xx[j] = xv[idx[j]];
+                p[j] = pv[idx[j]];
+                r[j] = rv[idx[j]];
+                q[j] = qv[idx[j]];
+                w[j] = invd[idx[j]];
             }
 #pragma unroll
         for (int j = 0; j < kU; ++j)
             if (idx[j] < n) {
-                xv[i[j]] = xx[j] + alpha * p[j];
+                xv[idx[j]] = xx[j] + alpha * p[j];
                 const T rn = r[j] - alpha * q[j];
-                rv[i[j]] = rn;
+                rv[idx[j]] = rn;
                 const T zz = rn * w[j];
                 a0 += rn * zz;
                 a1 += zz * zz;
@@ -459,21 +556,22 @@ __global__ void k_cgS_update(Dev g, const uint32_t* __restrict__ list, long long
 // ------------------------------------------------------------------------------------
 // per-component means (nullspace of S-hat_simple and S: constants per fluid component)
 // ------------------------------------------------------------------------------------
+// v is a dense cell vector (dense != 0: value at flist[m]) or a compact one (value at m).
 
 // Means of v over the (at most kMaxBig) big components, summed by the whole grid.
 template <typename T>
-__global__ void k_comp_big(Dev g, const int* __restrict__ cmp, const T* __restrict__ v,
-                           double* __restrict__ cmean, int nbig, Ctl* ctl,
+__global__ void k_comp_big(Dev g, Compact C, const int* __restrict__ cmpc, const T* __restrict__ v,
+                           int dense, double* __restrict__ cmean, int nbig, Ctl* ctl,
                            const CgState* outer, double* partials) {
     count_launch(ctl);
     if (outer->skip_next) return;
     double s[kMaxBig];
 #pragma unroll
     for (int b = 0; b < kMaxBig; ++b) s[b] = 0.0;
-    STREAM_LOOP(c, g.ncell) {
-        const int k = cmp[c];
-        if (k >= 0 && k < nbig) {
-            const double vc = (double)v[c];
+    STREAM_LOOP(m, C.n_p) {
+        const int k = cmpc[m];
+        if (k < nbig) {
+            const double vc = (double)(dense ? v[C.flist[m]] : v[m]);
 #pragma unroll
             for (int b = 0; b < kMaxBig; ++b) s[b] += (k == b) ? vc : 0.0;
         }
@@ -485,9 +583,9 @@ __global__ void k_comp_big(Dev g, const int* __restrict__ cmp, const T* __restri
 
 // Means of v over the small components, one warp per component (cells in fixed order).
 template <typename T>
-__global__ void k_comp_small(const int* __restrict__ start, const int* __restrict__ cells,
-                             const T* __restrict__ v, double* __restrict__ cmean, int nbig,
-                             int nsmall, Ctl* ctl, const CgState* outer) {
+__global__ void k_comp_small(Compact C, const int* __restrict__ start, const int* __restrict__ cells,
+                             const T* __restrict__ v, int dense, double* __restrict__ cmean,
+                             int nbig, int nsmall, Ctl* ctl, const CgState* outer) {
     count_launch(ctl);
     if (outer->skip_next) return;
     const int lane = threadIdx.x & 31;
@@ -496,19 +594,38 @@ __global__ void k_comp_small(const int* __restrict__ start, const int* __restric
          j += (long long)gridDim.x * warps) {
         const int b0 = start[j], b1 = start[j + 1];
         double s = 0.0;
-        for (int i = b0 + lane; i < b1; i += 32) s += (double)v[cells[i]];
+        for (int i = b0 + lane; i < b1; i += 32) {
+            const int m = cells[i];
+            s += (double)(dense ? v[C.flist[m]] : v[m]);
+        }
         s = warp_sum(s);
         if (lane == 0) cmean[nbig + j] = s / (double)(b1 - b0);
     }
 }
 
+// B u = -h^-1 sum_a (u_(a, c+e_a) - u_(a, c)) at fluid cell (x, y, z) from a compact face
+// vector, and the sum of the magnitudes of its terms.
+template <typename TX>
+__device__ __forceinline__ double div_at(const Dev& g, const Compact& C, const TX* __restrict__ u,
+                                         int x, int y, int z, double* mag) {
+    double s = 0.0, sa = 0.0;
+    for (int a = 0; a < g.d; ++a) {
+        const double up = face_valc(g, C, u, a, x + (a == 0), y + (a == 1), z + (a == 2));
+        const double lo = face_valc(g, C, u, a, x, y, z);
+        s += up - lo;
+        sa += fabs(up) + fabs(lo);
+    }
+    if (mag) *mag = g.hinv * sa;
+    return -g.hinv * s;
+}
+
 // ------------------------------------------------------------------------------------
-// outer Schur CG (Algorithm 1), cell space, FP64
+// outer Schur CG (Algorithm 1), dense cell space, FP64
 // ------------------------------------------------------------------------------------
 
 // g = B u (u = A^-1 f); r = g, p = 0, d = g; zero-RHS test.
 template <typename TX>
-__global__ void k_outer_init(Dev g, const uint8_t* __restrict__ mask, const uint8_t* __restrict__ flags,
+__global__ void k_outer_init(Dev g, Compact C, const uint8_t* __restrict__ mask,
                              const TX* __restrict__ u, double* __restrict__ gv,
                              double* __restrict__ rv, double* __restrict__ pv,
                              double* __restrict__ dv, Ctl* ctl, double* partials, int slot) {
@@ -517,18 +634,10 @@ __global__ void k_outer_init(Dev g, const uint8_t* __restrict__ mask, const uint
     TILE_LOOP_BEGIN(g)
         double gc = 0.0;
         if (mask[c] == 1) {
-            double s = 0.0, sa = 0.0;
-            for (int a = 0; a < g.d; ++a) {
-                int ex, ey, ez;
-                axis_step(a, 1, ex, ey, ez);
-                const double up = face_val(g, flags, u, a, x + ex, y + ey, z + ez);
-                const double lo = face_val(g, flags, u, a, x, y, z);
-                s += up - lo;
-                sa += fabs(up) + fabs(lo);
-            }
-            gc = -g.hinv * s;
+            double mag;
+            gc = div_at(g, C, u, x, y, z, &mag);
             v[0] += gc * gc;
-            v[1] += (g.hinv * sa) * (g.hinv * sa);
+            v[1] += mag * mag;
         }
         gv[c] = gc;
         rv[c] = gc;
@@ -560,15 +669,16 @@ __global__ void k_outer_init(Dev g, const uint8_t* __restrict__ mask, const uint
 
 // SIMPLE: z_0 = S-hat^-1 r_0 minus its component means; d = z_0, rho = r.z, ||z_0||^2.
 template <typename TX>
-__global__ void k_outer_start(Dev g, const int* __restrict__ cmp, const double* __restrict__ cmean,
-                              const TX* __restrict__ sx, const double* __restrict__ rv,
-                              double* __restrict__ dv, Ctl* ctl, double* partials, int slot) {
+__global__ void k_outer_start(Dev g, Compact C, const int* __restrict__ cmpc,
+                              const double* __restrict__ cmean, const TX* __restrict__ sx,
+                              const double* __restrict__ rv, double* __restrict__ dv, Ctl* ctl,
+                              double* partials, int slot) {
     count_launch(ctl);
     if (ctl->out.done) return;
     double v[2] = {0.0, 0.0};
-    STREAM_LOOP(c, g.ncell) {
-        const int k = cmp[c];
-        const double zc = (k >= 0) ? (double)sx[c] - cmean[k] : 0.0;
+    STREAM_LOOP(m, C.n_p) {
+        const uint32_t c = C.flist[m];
+        const double zc = (double)sx[m] - cmean[cmpc[m]];
         dv[c] = zc;
         v[0] += rv[c] * zc;
         v[1] += zc * zc;
@@ -588,7 +698,7 @@ __global__ void k_outer_start(Dev g, const int* __restrict__ cmp, const double* 
 
 // q = B u with u = A^-1 B^T d; alpha = rho / d.q.
 template <typename TX>
-__global__ void k_outer_div(Dev g, const uint8_t* __restrict__ mask, const uint8_t* __restrict__ flags,
+__global__ void k_outer_div(Dev g, Compact C, const uint8_t* __restrict__ mask,
                             const TX* __restrict__ u, const double* __restrict__ dv,
                             double* __restrict__ qv, Ctl* ctl, double* partials, int slot) {
     count_launch(ctl);
@@ -596,13 +706,7 @@ __global__ void k_outer_div(Dev g, const uint8_t* __restrict__ mask, const uint8
     TILE_LOOP_BEGIN(g)
         double qc = 0.0;
         if (mask[c] == 1) {
-            double s = 0.0;
-            for (int a = 0; a < g.d; ++a) {
-                int ex, ey, ez;
-                axis_step(a, 1, ex, ey, ez);
-                s += face_val(g, flags, u, a, x + ex, y + ey, z + ez) - face_val(g, flags, u, a, x, y, z);
-            }
-            qc = -g.hinv * s;
+            qc = div_at(g, C, u, x, y, z, nullptr);
             v[0] += dv[c] * qc;
         }
         qv[c] = qc;
@@ -684,17 +788,16 @@ __global__ void k_outer_update(Dev g, double* __restrict__ pv, double* __restric
 // SIMPLE: z = S-hat^-1 r minus its component means; rho' = r.z, ||z||; preconditioned
 // test; beta.
 template <typename TX>
-__global__ void k_outer_dots(Dev g, const int* __restrict__ cmp, const double* __restrict__ cmean,
-                             const TX* __restrict__ sx, const double* __restrict__ rv,
-                             Ctl* ctl, double* partials, int slot) {
+__global__ void k_outer_dots(Dev g, Compact C, const int* __restrict__ cmpc,
+                             const double* __restrict__ cmean, const TX* __restrict__ sx,
+                             const double* __restrict__ rv, Ctl* ctl, double* partials, int slot) {
     count_launch(ctl);
     CgState* o = &ctl->out;
     if (o->done) return;
     double v[2] = {0.0, 0.0};
-    STREAM_LOOP(c, g.ncell) {
-        const int k = cmp[c];
-        const double zc = (k >= 0) ? (double)sx[c] - cmean[k] : 0.0;
-        v[0] += rv[c] * zc;
+    STREAM_LOOP(m, C.n_p) {
+        const double zc = (double)sx[m] - cmean[cmpc[m]];
+        v[0] += rv[C.flist[m]] * zc;
         v[1] += zc * zc;
     }
     if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0()) {
@@ -719,9 +822,10 @@ __global__ void k_outer_dots(Dev g, const int* __restrict__ cmp, const double* _
 
 // d = z + beta d (Uzawa: z = r).  `gate` is out.done for PCG and out.skip_next for FCG.
 template <typename TX>
-__global__ void k_outer_dir(Dev g, const int* __restrict__ cmp, const double* __restrict__ cmean,
-                            const TX* __restrict__ sx, const double* __restrict__ rv,
-                            double* __restrict__ dv, Ctl* ctl, const int* gate) {
+__global__ void k_outer_dir(Dev g, Compact C, const int* __restrict__ cmpc,
+                            const double* __restrict__ cmean, const TX* __restrict__ sx,
+                            const double* __restrict__ rv, double* __restrict__ dv, Ctl* ctl,
+                            const int* gate) {
     count_launch(ctl);
     const CgState* o = &ctl->out;
     if (*gate) return;
@@ -729,9 +833,9 @@ __global__ void k_outer_dir(Dev g, const int* __restrict__ cmp, const double* __
     if (ctl->precond == 0) {
         STREAM_LOOP(c, g.ncell) dv[c] = rv[c] + beta * dv[c];
     } else {
-        STREAM_LOOP(c, g.ncell) {
-            const int k = cmp[c];
-            const double zc = (k >= 0) ? (double)sx[c] - cmean[k] : 0.0;
+        STREAM_LOOP(m, C.n_p) {
+            const uint32_t c = C.flist[m];
+            const double zc = (double)sx[m] - cmean[cmpc[m]];
             dv[c] = zc + beta * dv[c];
         }
     }
@@ -743,22 +847,18 @@ __global__ void k_outer_dir(Dev g, const int* __restrict__ cmp, const double* __
 
 // Start of a refinement step: d = z_0 (Uzawa: r), ||r||^2 of the step's true residual.
 template <typename TX>
-__global__ void k_fcg_start(Dev g, const int* __restrict__ cmp, const double* __restrict__ cmean,
-                            const TX* __restrict__ sx, const double* __restrict__ rv,
-                            double* __restrict__ dv, Ctl* ctl, double* partials, int slot) {
+__global__ void k_fcg_start(Dev g, Compact C, const int* __restrict__ cmpc,
+                            const double* __restrict__ cmean, const TX* __restrict__ sx,
+                            const double* __restrict__ rv, double* __restrict__ dv, Ctl* ctl,
+                            double* partials, int slot) {
     count_launch(ctl);
     double v[1] = {0.0};
     const int simple = ctl->precond == 1;
-    STREAM_LOOP(c, g.ncell) {
-        double zc;
-        if (simple) {
-            const int k = cmp[c];
-            zc = (k >= 0) ? (double)sx[c] - cmean[k] : 0.0;
-        } else {
-            zc = rv[c];
-        }
-        dv[c] = zc;
-        v[0] += rv[c] * rv[c];
+    STREAM_LOOP(m, C.n_p) {
+        const uint32_t c = C.flist[m];
+        const double rc = rv[c];
+        dv[c] = simple ? (double)sx[m] - cmean[cmpc[m]] : rc;
+        v[0] += rc * rc;
     }
     if (reduce_last_block<1>(v, partials, &ctl->ticket) && is_thread0()) {
         ctl->mix.rr_step0 = v[0];
@@ -770,7 +870,7 @@ __global__ void k_fcg_start(Dev g, const int* __restrict__ cmp, const double* __
 
 // q = B u (u = A^-1 B^T d in T); alpha = d.r / d.q (flexible CG).
 template <typename TX>
-__global__ void k_fcg_div(Dev g, const uint8_t* __restrict__ mask, const uint8_t* __restrict__ flags,
+__global__ void k_fcg_div(Dev g, Compact C, const uint8_t* __restrict__ mask,
                           const TX* __restrict__ u, const double* __restrict__ dv,
                           const double* __restrict__ rv, double* __restrict__ qv, Ctl* ctl,
                           double* partials, int slot, int slot_ref) {
@@ -779,13 +879,7 @@ __global__ void k_fcg_div(Dev g, const uint8_t* __restrict__ mask, const uint8_t
     TILE_LOOP_BEGIN(g)
         double qc = 0.0;
         if (mask[c] == 1) {
-            double s = 0.0;
-            for (int a = 0; a < g.d; ++a) {
-                int ex, ey, ez;
-                axis_step(a, 1, ex, ey, ez);
-                s += face_val(g, flags, u, a, x + ex, y + ey, z + ez) - face_val(g, flags, u, a, x, y, z);
-            }
-            qc = -g.hinv * s;
+            qc = div_at(g, C, u, x, y, z, nullptr);
             v[0] += dv[c] * qc;
             v[1] += dv[c] * rv[c];
         }
@@ -842,22 +936,18 @@ __global__ void k_fcg_update(Dev g, double* __restrict__ pv, double* __restrict_
 
 // FCG(1) direction coefficient: beta = -z.q / d.q (z with its component means removed).
 template <typename TX>
-__global__ void k_fcg_dots(Dev g, const int* __restrict__ cmp, const double* __restrict__ cmean,
-                           const TX* __restrict__ sx, const double* __restrict__ rv,
-                           const double* __restrict__ qv, Ctl* ctl, double* partials) {
+__global__ void k_fcg_dots(Dev g, Compact C, const int* __restrict__ cmpc,
+                           const double* __restrict__ cmean, const TX* __restrict__ sx,
+                           const double* __restrict__ rv, const double* __restrict__ qv,
+                           Ctl* ctl, double* partials) {
     count_launch(ctl);
     CgState* o = &ctl->out;
     if (o->skip_next) return;
     const int simple = ctl->precond == 1;
     double v[1] = {0.0};
-    STREAM_LOOP(c, g.ncell) {
-        double zc;
-        if (simple) {
-            const int k = cmp[c];
-            zc = (k >= 0) ? (double)sx[c] - cmean[k] : 0.0;
-        } else {
-            zc = rv[c];
-        }
+    STREAM_LOOP(m, C.n_p) {
+        const uint32_t c = C.flist[m];
+        const double zc = simple ? (double)sx[m] - cmean[cmpc[m]] : rv[c];
         v[0] += zc * qv[c];
     }
     if (reduce_last_block<1>(v, partials, &ctl->ticket) && is_thread0())
@@ -866,7 +956,7 @@ __global__ void k_fcg_dots(Dev g, const int* __restrict__ cmp, const double* __r
 
 // True residual r = g - B u with u = A^-1 B^T p from an FP64 inner solve; decides whether
 // another refinement step follows.
-__global__ void k_true_res(Dev g, const uint8_t* __restrict__ mask, const uint8_t* __restrict__ flags,
+__global__ void k_true_res(Dev g, Compact C, const uint8_t* __restrict__ mask,
                            const double* __restrict__ u, const double* __restrict__ gv,
                            double* __restrict__ rv, Ctl* ctl, double* partials, int slot_ref) {
     count_launch(ctl);
@@ -875,13 +965,7 @@ __global__ void k_true_res(Dev g, const uint8_t* __restrict__ mask, const uint8_
     TILE_LOOP_BEGIN(g)
         double rc = 0.0;
         if (mask[c] == 1) {
-            double s = 0.0;
-            for (int a = 0; a < g.d; ++a) {
-                int ex, ey, ez;
-                axis_step(a, 1, ex, ey, ez);
-                s += face_val(g, flags, u, a, x + ex, y + ey, z + ez) - face_val(g, flags, u, a, x, y, z);
-            }
-            rc = gv[c] + g.hinv * s;  // g - B u with B u = -h^-1 sum
+            rc = gv[c] - div_at(g, C, u, x, y, z, nullptr);
             v[0] += rc * rc;
         }
         rv[c] = rc;
@@ -907,16 +991,17 @@ __global__ void k_true_res(Dev g, const uint8_t* __restrict__ mask, const uint8_
     }
 }
 
-// u = x (the recovered velocity) and the per-axis sums of u for the permeability.
-__global__ void k_copy_u(Dev g, const uint8_t* __restrict__ flags, const double* __restrict__ xv,
-                         double* __restrict__ u, Ctl* ctl, double* partials) {
+// u = x scattered to the dense face layout, and the per-axis sums for the permeability.
+__global__ void k_copy_u(Dev g, Compact C, const double* __restrict__ xv, double* __restrict__ u,
+                         Ctl* ctl, double* partials) {
     count_launch(ctl);
     double v[3] = {0.0, 0.0, 0.0};
-    const long long n = (long long)g.d * g.stride;
-    STREAM_LOOP(i, n) {
-        const double xi = (flags[i] & 1) ? xv[i] : 0.0;
+    const uint32_t s = (uint32_t)g.stride;
+    STREAM_LOOP(k, C.n_u) {
+        const uint32_t i = C.ulist[k];
+        const double xi = xv[k];
         u[i] = xi;
-        const int a = (int)(i / g.stride);
+        const int a = (i >= s) + (i >= 2u * s);
         v[0] += (a == 0) ? xi : 0.0;
         v[1] += (a == 1) ? xi : 0.0;
         v[2] += (a == 2) ? xi : 0.0;
@@ -941,19 +1026,25 @@ static inline dim3 sgrid(const Handle& H, long long n) {
     return dim3((unsigned)(nb < H.target_blocks ? (nb > 0 ? nb : 1) : H.target_blocks));
 }
 static inline dim3 sblock() { return dim3(kBlock); }
-// column-tile grid: x = strided x-y tiles, y = z chunks, z = fields
-static inline dim3 cgrid(const Handle& H, int fields) {
-    const long long tiles = (long long)((H.g.nx + kTileX - 1) / kTileX) * ((H.g.ny + kTileY - 1) / kTileY);
-    const long long target = H.target_blocks;
-    long long zs = 1, gxx = tiles;
-    if (tiles * fields >= target) {
-        gxx = (target + fields - 1) / fields;
-    } else {
-        zs = (target + tiles * fields - 1) / (tiles * fields);
-        if (zs > H.g.nz) zs = H.g.nz;
-    }
-    if (gxx < 1) gxx = 1;
-    return dim3((unsigned)gxx, (unsigned)zs, (unsigned)fields);
+
+static Compact compact_of(const Handle& H) {
+    Compact C;
+    C.ulist = H.ulist;
+    C.flist = H.flist;
+    C.ufl = H.ufl;
+    C.fmask = H.fmask;
+    C.fbase = H.fbase;
+    C.cmask = H.cmask;
+    C.cbase = H.cbase;
+    C.W = H.W;
+    C.n_u = H.n_u;
+    C.n_p = H.n_p;
+    C.nbA = H.nbA;
+    C.nbS = H.nbS;
+    C.codeS = H.codeS;
+    C.ldA = H.ldA;
+    C.ldS = H.ldS;
+    return C;
 }
 
 // Buffers of one inner solve.
@@ -965,62 +1056,66 @@ template <typename T>
 struct InnerS {
     T *x, *r, *p, *q;
     const T* invd;
+    const T* diag;   // diagonal of S-hat (read by the FP64 matvec only)
 };
 static InnerA<double> innerA64(Handle& H) { return {H.ax, H.ar, H.ap, H.aq}; }
 static InnerA<float> innerA32(Handle& H) { return {H.axf, H.arf, H.apf, H.aqf}; }
-static InnerS<double> innerS64(Handle& H) { return {H.sx, H.sr, H.sp, H.sq, H.invdS}; }
-static InnerS<float> innerS32(Handle& H) { return {H.sxf, H.srf, H.spf, H.sqf, H.invdSf}; }
+static InnerS<double> innerS64(Handle& H) { return {H.sx, H.sr, H.sp, H.sq, H.invdSc, H.dSc}; }
+static InnerS<float> innerS32(Handle& H) { return {H.sxf, H.srf, H.spf, H.sqf, H.invdSf, nullptr}; }
 
 // x = A^-1 b with b = cf f + cp B^T P (+ bvec) formed by k_cgA_init.
 template <typename T>
 static void record_A_solve(Handle& H, Recorder& R, InnerA<T> v, CgState* st, int s,
                            const double* P, double cp, double cf, const double* bvec) {
-    R.launch("cgA_init", k_cgA_init<T>, cgrid(H, H.g.d), tblock(), H.g, (const uint8_t*)H.flags,
-             v.x, v.r, P, cp, cf, bvec, H.dctl, st, H.partials, s);
+    const Compact C = compact_of(H);
     const long long nu = H.n_u;
-    R.loop(s, [&H, v, st, s, nu](Recorder& B) {
-        B.launch("cgA_dir", k_cgA_dir<T>, sgrid(H, nu), sblock(), H.g, (const uint32_t*)H.ulist, nu,
-                 (const uint8_t*)H.flags, (const T*)v.r, v.p, H.dctl, (const CgState*)st);
-        B.launch("cgA_matvec", k_cgA_matvec<T>, sgrid(H, nu), sblock(), H.g, (const uint32_t*)H.ulist,
-                 nu, (const uint8_t*)H.flags, (const T*)v.p, v.q, H.dctl, st, H.partials, s);
-        B.launch("cgA_update", k_cgA_update<T>, sgrid(H, nu), sblock(), H.g, (const uint32_t*)H.ulist,
-                 nu, (const uint8_t*)H.flags, v.x, v.r, (const T*)v.p, (const T*)v.q, H.dctl, st,
+    R.launch("cgA_init", k_cgA_init<T>, sgrid(H, nu), sblock(), H.g, C, v.x, v.r, P, cp, cf,
+             bvec, H.dctl, st, H.partials, s);
+    R.loop(s, [&H, C, v, st, s, nu](Recorder& B) {
+        B.launch("cgA_dir", k_cgA_dir<T>, sgrid(H, nu), sblock(), H.g, nu, (const uint8_t*)H.ufl,
+                 (const T*)v.r, v.p, H.dctl, (const CgState*)st);
+        B.launch("cgA_matvec", k_cgA_matvec<T>, sgrid(H, nu), sblock(), H.g, C, (const T*)v.p, v.q,
+                 H.dctl, st, H.partials, s);
+        B.launch("cgA_update", k_cgA_update<T>, sgrid(H, nu), sblock(), H.g, nu,
+                 (const uint8_t*)H.ufl, v.x, v.r, (const T*)v.p, (const T*)v.q, H.dctl, st,
                  H.partials, s);
     });
 }
 
 template <typename T>
-static void record_comp_means(Handle& H, Recorder& R, const T* v) {
+static void record_comp_means(Handle& H, Recorder& R, const T* v, int dense) {
     const CgState* outer = &H.dctl->out;
-    R.launch("comp_big", k_comp_big<T>, sgrid(H, H.g.ncell), sblock(), H.g, (const int*)H.cmp, v,
-             H.cmean, H.n_big, H.dctl, outer, H.partials);
+    const Compact C = compact_of(H);
+    R.launch("comp_big", k_comp_big<T>, sgrid(H, H.n_p), sblock(), H.g, C, (const int*)H.cmpc, v,
+             dense, H.cmean, H.n_big, H.dctl, outer, H.partials);
     if (H.n_small > 0) {
         const long long nb = (H.n_small + 7) / 8;
         const dim3 grid((unsigned)(nb < H.target_blocks ? nb : H.target_blocks));
-        R.launch("comp_small", k_comp_small<T>, grid, sblock(), (const int*)H.small_start,
-                 (const int*)H.small_cells, v, H.cmean, H.n_big, H.n_small, H.dctl, outer);
+        R.launch("comp_small", k_comp_small<T>, grid, sblock(), C, (const int*)H.small_start,
+                 (const int*)H.small_cells, v, dense, H.cmean, H.n_big, H.n_small, H.dctl, outer);
     }
 }
 
-// z = S-hat^+ r: r (the FP64 outer residual) is projected onto the range (component
-// means removed, in place), the inner CG runs in T, and the per-component means of the
-// solution are left in cmean for the consumers to subtract.
+// z = S-hat^+ r: r (the dense FP64 outer residual) is projected onto the range (component
+// means removed, in place), the inner CG runs in T on compact vectors, and the
+// per-component means of the solution are left in cmean for the consumers to subtract.
 template <typename T>
 static void record_S_solve(Handle& H, Recorder& R, InnerS<T> v, CgState* st, int s) {
-    record_comp_means<double>(H, R, H.orr);
-    R.launch("cgS_init", k_cgS_init<T>, sgrid(H, H.g.ncell), sblock(), H.g, v.invd,
-             (const int*)H.cmp, (const double*)H.cmean, H.orr, v.x, v.r, H.dctl, st,
-             (const CgState*)&H.dctl->out, H.partials, s);
+    const Compact C = compact_of(H);
     const long long np = H.n_p;
-    R.loop(s, [&H, v, st, s, np](Recorder& B) {
-        B.launch("cgS_dir", k_cgS_dir<T>, sgrid(H, np), sblock(), H.g, (const uint32_t*)H.flist, np,
-                 v.invd, (const T*)v.r, v.p, H.dctl, (const CgState*)st);
-        B.launch("cgS_matvec", k_cgS_matvec<T>, sgrid(H, np), sblock(), H.g, (const uint32_t*)H.flist,
-                 np, (const uint8_t*)H.flags, (const T*)v.p, v.q, H.dctl, st, H.partials, s);
-        B.launch("cgS_update", k_cgS_update<T>, sgrid(H, np), sblock(), H.g, (const uint32_t*)H.flist,
-                 np, v.invd, v.x, v.r, (const T*)v.p, (const T*)v.q, H.dctl, st, H.partials, s);
+    record_comp_means<double>(H, R, H.orr, 1);
+    R.launch("cgS_init", k_cgS_init<T>, sgrid(H, np), sblock(), H.g, C, v.invd,
+             (const int*)H.cmpc, (const double*)H.cmean, H.orr, v.x, v.r, H.dctl, st,
+             (const CgState*)&H.dctl->out, H.partials, s);
+    R.loop(s, [&H, C, v, st, s, np](Recorder& B) {
+        B.launch("cgS_dir", k_cgS_dir<T>, sgrid(H, np), sblock(), H.g, np, v.invd, (const T*)v.r,
+                 v.p, H.dctl, (const CgState*)st);
+        B.launch("cgS_matvec", k_cgS_matvec<T>, sgrid(H, np), sblock(), H.g, C,
+                 v.diag, (const T*)v.p, v.q, H.dctl, st, H.partials, s);
+        B.launch("cgS_update", k_cgS_update<T>, sgrid(H, np), sblock(), H.g, np, v.invd, v.x, v.r,
+                 (const T*)v.p, (const T*)v.q, H.dctl, st, H.partials, s);
     });
-    record_comp_means<T>(H, R, (const T*)v.x);
+    record_comp_means<T>(H, R, (const T*)v.x, 0);
 }
 
 // Algorithm 1 in FP64.
@@ -1030,6 +1125,7 @@ static void record_solve_fp64(Handle& H, Recorder& R, int precond) {
     CgState* inS = &ctl->inS;
     const InnerA<double> A = innerA64(H);
     const InnerS<double> S = innerS64(H);
+    const Compact C = compact_of(H);
     // slots are allocated before any loop body is recorded: in host-driven mode a body
     // runs once per iteration and must not allocate
     const int s_rhs = R.new_slot();
@@ -1038,32 +1134,30 @@ static void record_solve_fp64(Handle& H, Recorder& R, int precond) {
     const int s_a = R.new_slot();
     const int s_s = R.new_slot();
     record_A_solve<double>(H, R, A, inA, s_rhs, nullptr, 0.0, 1.0, nullptr);   // A^-1 f
-    R.launch("outer_init", k_outer_init<double>, tgrid(H), tblock(), H.g, (const uint8_t*)H.mask,
-             (const uint8_t*)H.flags, (const double*)A.x, H.og, H.orr, H.op, H.od, ctl, H.partials,
-             s_out);
+    R.launch("outer_init", k_outer_init<double>, tgrid(H), tblock(), H.g, C, (const uint8_t*)H.mask,
+             (const double*)A.x, H.og, H.orr, H.op, H.od, ctl, H.partials, s_out);
     if (precond == 1) {
         record_S_solve<double>(H, R, S, inS, s_s0);
-        R.launch("outer_start", k_outer_start<double>, sgrid(H, H.g.ncell), sblock(), H.g,
-                 (const int*)H.cmp, (const double*)H.cmean, (const double*)S.x,
+        R.launch("outer_start", k_outer_start<double>, sgrid(H, H.n_p), sblock(), H.g, C,
+                 (const int*)H.cmpc, (const double*)H.cmean, (const double*)S.x,
                  (const double*)H.orr, H.od, ctl, H.partials, s_out);
     }
-    R.loop(s_out, [&H, ctl, inA, inS, A, S, precond, s_out, s_a, s_s](Recorder& B) {
+    R.loop(s_out, [&H, C, ctl, inA, inS, A, S, precond, s_out, s_a, s_s](Recorder& B) {
         // q = S d = B A^-1 B^T d
         record_A_solve<double>(H, B, A, inA, s_a, H.od, 1.0, 0.0, nullptr);
-        B.launch("outer_div", k_outer_div<double>, tgrid(H), tblock(), H.g, (const uint8_t*)H.mask,
-                 (const uint8_t*)H.flags, (const double*)A.x, (const double*)H.od, H.oq, ctl,
-                 H.partials, s_out);
+        B.launch("outer_div", k_outer_div<double>, tgrid(H), tblock(), H.g, C, (const uint8_t*)H.mask,
+                 (const double*)A.x, (const double*)H.od, H.oq, ctl, H.partials, s_out);
         B.launch("outer_update", k_outer_update, sgrid(H, H.g.ncell), sblock(), H.g, H.op, H.orr,
                  (const double*)H.od, (const double*)H.oq, ctl, H.partials, s_out);
         if (precond == 1) {
             record_S_solve<double>(H, B, S, inS, s_s);
-            B.launch("outer_dots", k_outer_dots<double>, sgrid(H, H.g.ncell), sblock(), H.g,
-                     (const int*)H.cmp, (const double*)H.cmean, (const double*)S.x,
+            B.launch("outer_dots", k_outer_dots<double>, sgrid(H, H.n_p), sblock(), H.g, C,
+                     (const int*)H.cmpc, (const double*)H.cmean, (const double*)S.x,
                      (const double*)H.orr, ctl, H.partials, s_out);
         }
-        B.launch("outer_dir", k_outer_dir<double>, sgrid(H, H.g.ncell), sblock(), H.g,
-                 (const int*)H.cmp, (const double*)H.cmean, (const double*)S.x, (const double*)H.orr,
-                 H.od, ctl, (const int*)&ctl->out.done);
+        B.launch("outer_dir", k_outer_dir<double>, sgrid(H, H.g.ncell), sblock(), H.g, C,
+                 (const int*)H.cmpc, (const double*)H.cmean, (const double*)S.x,
+                 (const double*)H.orr, H.od, ctl, (const int*)&ctl->out.done);
     });
 }
 
@@ -1073,6 +1167,7 @@ static void record_solve_mixed(Handle& H, Recorder& R, int precond) {
     const InnerA<double> A64 = innerA64(H);
     const InnerA<float> A32 = innerA32(H);
     const InnerS<float> S32 = innerS32(H);
+    const Compact C = compact_of(H);
     CgState* inA = &ctl->inA;
     CgState* inA32 = &ctl->inA32;
     CgState* inS32 = &ctl->inS32;
@@ -1084,36 +1179,34 @@ static void record_solve_mixed(Handle& H, Recorder& R, int precond) {
     const int s_s = R.new_slot();
     const int s_t = R.new_slot();
     record_A_solve<double>(H, R, A64, inA, s_rhs, nullptr, 0.0, 1.0, nullptr);  // FP64 A^-1 f
-    R.launch("outer_init", k_outer_init<double>, tgrid(H), tblock(), H.g, (const uint8_t*)H.mask,
-             (const uint8_t*)H.flags, (const double*)A64.x, H.og, H.orr, H.op, H.od, ctl,
-             H.partials, s_ref);
-    R.loop(s_ref, [&H, ctl, A64, A32, S32, inA, inA32, inS32, precond, s_ref, s_s0, s_fcg, s_a,
+    R.launch("outer_init", k_outer_init<double>, tgrid(H), tblock(), H.g, C, (const uint8_t*)H.mask,
+             (const double*)A64.x, H.og, H.orr, H.op, H.od, ctl, H.partials, s_ref);
+    R.loop(s_ref, [&H, C, ctl, A64, A32, S32, inA, inA32, inS32, precond, s_ref, s_s0, s_fcg, s_a,
                    s_s, s_t](Recorder& B) {
         if (precond == 1) record_S_solve<float>(H, B, S32, inS32, s_s0);
-        B.launch("fcg_start", k_fcg_start<float>, sgrid(H, H.g.ncell), sblock(), H.g,
-                 (const int*)H.cmp, (const double*)H.cmean, (const float*)S32.x,
+        B.launch("fcg_start", k_fcg_start<float>, sgrid(H, H.n_p), sblock(), H.g, C,
+                 (const int*)H.cmpc, (const double*)H.cmean, (const float*)S32.x,
                  (const double*)H.orr, H.od, ctl, H.partials, s_fcg);
-        B.loop(s_fcg, [&H, ctl, A32, S32, inA32, inS32, precond, s_fcg, s_a, s_s,
-                       s_ref](Recorder& C) {
-            record_A_solve<float>(H, C, A32, inA32, s_a, H.od, 1.0, 0.0, nullptr);
-            C.launch("fcg_div", k_fcg_div<float>, tgrid(H), tblock(), H.g, (const uint8_t*)H.mask,
-                     (const uint8_t*)H.flags, (const float*)A32.x, (const double*)H.od,
-                     (const double*)H.orr, H.oq, ctl, H.partials, s_fcg, s_ref);
-            C.launch("fcg_update", k_fcg_update, sgrid(H, H.g.ncell), sblock(), H.g, H.op, H.orr,
+        B.loop(s_fcg, [&H, C, ctl, A32, S32, inA32, inS32, precond, s_fcg, s_a, s_s,
+                       s_ref](Recorder& D) {
+            record_A_solve<float>(H, D, A32, inA32, s_a, H.od, 1.0, 0.0, nullptr);
+            D.launch("fcg_div", k_fcg_div<float>, tgrid(H), tblock(), H.g, C, (const uint8_t*)H.mask,
+                     (const float*)A32.x, (const double*)H.od, (const double*)H.orr, H.oq, ctl,
+                     H.partials, s_fcg, s_ref);
+            D.launch("fcg_update", k_fcg_update, sgrid(H, H.g.ncell), sblock(), H.g, H.op, H.orr,
                      (const double*)H.od, (const double*)H.oq, ctl, H.partials, s_fcg);
-            if (precond == 1) record_S_solve<float>(H, C, S32, inS32, s_s);
-            C.launch("fcg_dots", k_fcg_dots<float>, sgrid(H, H.g.ncell), sblock(), H.g,
-                     (const int*)H.cmp, (const double*)H.cmean, (const float*)S32.x,
+            if (precond == 1) record_S_solve<float>(H, D, S32, inS32, s_s);
+            D.launch("fcg_dots", k_fcg_dots<float>, sgrid(H, H.n_p), sblock(), H.g, C,
+                     (const int*)H.cmpc, (const double*)H.cmean, (const float*)S32.x,
                      (const double*)H.orr, (const double*)H.oq, ctl, H.partials);
-            C.launch("fcg_dir", k_outer_dir<float>, sgrid(H, H.g.ncell), sblock(), H.g,
-                     (const int*)H.cmp, (const double*)H.cmean, (const float*)S32.x,
+            D.launch("fcg_dir", k_outer_dir<float>, sgrid(H, H.g.ncell), sblock(), H.g, C,
+                     (const int*)H.cmpc, (const double*)H.cmean, (const float*)S32.x,
                      (const double*)H.orr, H.od, ctl, (const int*)&ctl->out.skip_next);
         });
         // true residual with an FP64 inner solve: r = g - B A^-1 B^T p
         record_A_solve<double>(H, B, A64, inA, s_t, H.op, 1.0, 0.0, nullptr);
-        B.launch("true_res", k_true_res, tgrid(H), tblock(), H.g, (const uint8_t*)H.mask,
-                 (const uint8_t*)H.flags, (const double*)A64.x, (const double*)H.og, H.orr, ctl,
-                 H.partials, s_ref);
+        B.launch("true_res", k_true_res, tgrid(H), tblock(), H.g, C, (const uint8_t*)H.mask,
+                 (const double*)A64.x, (const double*)H.og, H.orr, ctl, H.partials, s_ref);
     });
 }
 
@@ -1122,18 +1215,17 @@ void record_solve(Handle& H, Recorder& R, int precond, int precision) {
     else record_solve_fp64(H, R, precond);
 }
 
-void record_solve_recover(Handle& H, Recorder& R, int precond, int precision) {
-    record_solve(H, R, precond, precision);
-    record_recover(H, R);
-}
-
 void record_recover(Handle& H, Recorder& R) {
     Ctl* ctl = H.dctl;
     const int s = R.new_slot();
     record_A_solve<double>(H, R, innerA64(H), &ctl->rec, s, H.op, -1.0, 1.0, nullptr);
-    const long long nf = (long long)H.g.d * H.g.stride;
-    R.launch("copy_u", k_copy_u, sgrid(H, nf), sblock(), H.g, (const uint8_t*)H.flags,
+    R.launch("copy_u", k_copy_u, sgrid(H, H.n_u), sblock(), H.g, compact_of(H),
              (const double*)H.ax, H.u, ctl, H.partials);
+}
+
+void record_solve_recover(Handle& H, Recorder& R, int precond, int precision) {
+    record_solve(H, R, precond, precision);
+    record_recover(H, R);
 }
 
 void record_solve_A(Handle& H, Recorder& R, const double* b, double* x) {
@@ -1156,23 +1248,24 @@ cudaError_t time_kernel(Handle& H, int which, int slot, float* ms) {
     Ctl* ctl = H.dctl;
     CgState* st = &ctl->solo;
     const long long nu = H.n_u, np = H.n_p;
+    const Compact C = compact_of(H);
     cudaError_t e = cudaEventRecord(H.ev0, H.stream);
     if (e != cudaSuccess) return e;
     const dim3 gu = sgrid(H, nu), gp = sgrid(H, np), b = sblock();
     cudaStream_t s = H.stream;
     switch (which) {
-        case 0: k_cgA_dir<double><<<gu, b, 0, s>>>(H.g, H.ulist, nu, H.flags, H.ar, H.ap, ctl, st); break;
-        case 1: k_cgA_matvec<double><<<gu, b, 0, s>>>(H.g, H.ulist, nu, H.flags, H.ap, H.aq, ctl, st, H.partials, slot); break;
-        case 2: k_cgA_update<double><<<gu, b, 0, s>>>(H.g, H.ulist, nu, H.flags, H.ax, H.ar, H.ap, H.aq, ctl, st, H.partials, slot); break;
-        case 3: k_cgS_dir<double><<<gp, b, 0, s>>>(H.g, H.flist, np, H.invdS, H.sr, H.sp, ctl, st); break;
-        case 4: k_cgS_matvec<double><<<gp, b, 0, s>>>(H.g, H.flist, np, H.flags, H.sp, H.sq, ctl, st, H.partials, slot); break;
-        case 5: k_cgS_update<double><<<gp, b, 0, s>>>(H.g, H.flist, np, H.invdS, H.sx, H.sr, H.sp, H.sq, ctl, st, H.partials, slot); break;
-        case 6: k_cgA_dir<float><<<gu, b, 0, s>>>(H.g, H.ulist, nu, H.flags, H.arf, H.apf, ctl, st); break;
-        case 7: k_cgA_matvec<float><<<gu, b, 0, s>>>(H.g, H.ulist, nu, H.flags, H.apf, H.aqf, ctl, st, H.partials, slot); break;
-        case 8: k_cgA_update<float><<<gu, b, 0, s>>>(H.g, H.ulist, nu, H.flags, H.axf, H.arf, H.apf, H.aqf, ctl, st, H.partials, slot); break;
-        case 9: k_cgS_dir<float><<<gp, b, 0, s>>>(H.g, H.flist, np, H.invdSf, H.srf, H.spf, ctl, st); break;
-        case 10: k_cgS_matvec<float><<<gp, b, 0, s>>>(H.g, H.flist, np, H.flags, H.spf, H.sqf, ctl, st, H.partials, slot); break;
-        case 11: k_cgS_update<float><<<gp, b, 0, s>>>(H.g, H.flist, np, H.invdSf, H.sxf, H.srf, H.spf, H.sqf, ctl, st, H.partials, slot); break;
+        case 0: k_cgA_dir<double><<<gu, b, 0, s>>>(H.g, nu, H.ufl, H.ar, H.ap, ctl, st); break;
+        case 1: k_cgA_matvec<double><<<gu, b, 0, s>>>(H.g, C, H.ap, H.aq, ctl, st, H.partials, slot); break;
+        case 2: k_cgA_update<double><<<gu, b, 0, s>>>(H.g, nu, H.ufl, H.ax, H.ar, H.ap, H.aq, ctl, st, H.partials, slot); break;
+        case 3: k_cgS_dir<double><<<gp, b, 0, s>>>(H.g, np, H.invdSc, H.sr, H.sp, ctl, st); break;
+        case 4: k_cgS_matvec<double><<<gp, b, 0, s>>>(H.g, C, H.dSc, H.sp, H.sq, ctl, st, H.partials, slot); break;
+        case 5: k_cgS_update<double><<<gp, b, 0, s>>>(H.g, np, H.invdSc, H.sx, H.sr, H.sp, H.sq, ctl, st, H.partials, slot); break;
+        case 6: k_cgA_dir<float><<<gu, b, 0, s>>>(H.g, nu, H.ufl, H.arf, H.apf, ctl, st); break;
+        case 7: k_cgA_matvec<float><<<gu, b, 0, s>>>(H.g, C, H.apf, H.aqf, ctl, st, H.partials, slot); break;
+        case 8: k_cgA_update<float><<<gu, b, 0, s>>>(H.g, nu, H.ufl, H.axf, H.arf, H.apf, H.aqf, ctl, st, H.partials, slot); break;
+        case 9: k_cgS_dir<float><<<gp, b, 0, s>>>(H.g, np, H.invdSf, H.srf, H.spf, ctl, st); break;
+        case 10: k_cgS_matvec<float><<<gp, b, 0, s>>>(H.g, C, (const float*)nullptr, H.spf, H.sqf, ctl, st, H.partials, slot); break;
+        case 11: k_cgS_update<float><<<gp, b, 0, s>>>(H.g, np, H.invdSf, H.sxf, H.srf, H.spf, H.sqf, ctl, st, H.partials, slot); break;
         default: return cudaErrorInvalidValue;
     }
     e = cudaGetLastError();
@@ -1180,6 +1273,16 @@ cudaError_t time_kernel(Handle& H, int which, int slot, float* ms) {
     if (e == cudaSuccess) e = cudaEventSynchronize(H.ev1);
     if (e == cudaSuccess) e = cudaEventElapsedTime(ms, H.ev0, H.ev1);
     return e;
+}
+
+cudaError_t launch_build_tables(Handle& H) {
+    const Compact C = compact_of(H);
+    if (H.n_u > 0)
+        k_build_nbA<<<sgrid(H, H.n_u), sblock(), 0, H.stream>>>(H.g, C, H.nbA);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || H.n_p == 0) return e;
+    k_build_nbS<<<sgrid(H, H.n_p), sblock(), 0, H.stream>>>(H.g, C, H.flags, H.nbS, H.codeS, H.dSc);
+    return cudaGetLastError();
 }
 
 }  // namespace schur
