@@ -35,7 +35,8 @@ int cuda_error(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_error(e_, what);   \
     } while (0)
 
-constexpr int kHostSlotBase = 24;  // host-driven loops reuse slots 24..31 on every call
+constexpr int kHostSlotBase = 24;
+constexpr long long kMaxCompact = (1ll << 31) - (1ll << 24);  // host-driven loops reuse slots 24..31 on every call
 
 template <class T>
 cudaError_t alloc(Handle& H, T** p, size_t n) {
@@ -199,6 +200,9 @@ int build_components(Handle& H, const uint8_t* m) {
     }
     H.n_u = (long long)ul.size();
     H.n_p = (long long)fl.size();
+    // the inner kernels index compact vectors with 32-bit offsets (plus a grid's stride)
+    if (H.n_u > kMaxCompact || H.n_p > kMaxCompact)
+        return set_error(SCHUR_EINVAL, "more than 2^31 - 2^24 unknown faces or fluid cells");
     H.W = W;
     if (ul.empty()) ul.push_back(0);
     if (fl.empty()) { fl.push_back(0); cmpc.push_back(0); }

@@ -154,27 +154,30 @@ __device__ __forceinline__ double warp_sum(double x) {
 
 // Block-sum K doubles; every block writes its partial sums, and the block that finishes
 // last sums all partials in a fixed order (deterministic for a fixed grid), resets the
-// ticket and returns true with the totals in v[] for all its threads.
+// ticket and returns true with the totals in v[] for all its threads.  The block's
+// values go through shared memory so that one warp does the additions (8 per lane, then
+// a 5-step shuffle tree): on a part whose FP64 pipe retires 2 lanes per clock and SM, a
+// shuffle tree in every warp would cost several times the FP64 work.  Blocks have at
+// most kBlock threads, a multiple of 32.
 template <int K>
 __device__ __forceinline__ bool reduce_last_block(double (&v)[K], double* partials,
                                                   unsigned int* ticket) {
-    __shared__ double sm[K][32];
+    __shared__ double sm[K][kBlock];
     __shared__ unsigned int s_last;
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
     const int nthr = blockDim.x * blockDim.y * blockDim.z;
-    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    const int lane = tid & 31, warp = tid >> 5;
     const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
     const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        double x = warp_sum(v[k]);
-        if (lane == 0) sm[k][warp] = x;
-    }
+    for (int k = 0; k < K; ++k) sm[k][tid] = v[k];
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            double x = warp_sum(lane < nwarp ? sm[k][lane] : 0.0);
+            double x = 0.0;
+            for (int j = lane; j < nthr; j += 32) x += sm[k][j];
+            x = warp_sum(x);
             if (lane == 0) partials[(size_t)bid * K + k] = x;
         }
         if (lane == 0) {
@@ -193,19 +196,22 @@ __device__ __forceinline__ bool reduce_last_block(double (&v)[K], double* partia
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] += __ldcg(&partials[(size_t)i * K + k]);
     }
-    __syncthreads();
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        double x = warp_sum(acc[k]);
-        if (lane == 0) sm[k][warp] = x;
-    }
+    for (int k = 0; k < K; ++k) sm[k][tid] = acc[k];
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            double x = warp_sum(lane < nwarp ? sm[k][lane] : 0.0);
-            if (lane == 0) sm[k][0] = x;
+            double x = 0.0;
+            for (int j = lane; j < nthr; j += 32) x += sm[k][j];
+            x = warp_sum(x);
+            if (lane == 0) acc[k] = x;
         }
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) sm[k][0] = acc[k];
     }
     __syncthreads();
 #pragma unroll

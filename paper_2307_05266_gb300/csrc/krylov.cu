@@ -26,7 +26,10 @@
 // All scalars live in the device control block; every loop is a conditional while node
 // of one CUDA graph (or a host loop in debugging mode).  Every loop terminates: each
 // condition update either continues below its iteration cap or stops.
+#include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 
 #include "internal.h"
 
@@ -114,20 +117,23 @@ __device__ __forceinline__ void finish_matvec(Ctl* ctl, CgState* st, double dq, 
 // ------------------------------------------------------------------------------------
 // access patterns and the compact layout
 // ------------------------------------------------------------------------------------
-// Streaming kernels: a warp owns kU chunks of 32 consecutive compact entries per step
+// Streaming kernels: a warp owns U chunks of 32 consecutive compact entries per step
 // (lane l takes entry base + l + 32 j), every load is a coalesced row, and each thread
-// has kU independent loads in flight.
-constexpr int kU = 4;
+// has U independent loads in flight (4 in FP32; 2 in FP64, whose kernels are bound by
+// the FP64 pipe and gain more from resident warps than from deeper unrolling).
+template <typename T> struct StreamU { static constexpr int v = 4; };
+template <> struct StreamU<double> { static constexpr int v = 2; };
 
-#define WARP_STREAM_BEGIN(n)                                                              \
+// 32-bit indices: entry counts stay below 2^31 (checked when a geometry is created).
+#define WARP_STREAM_BEGIN_U(n, U)                                                         \
     {                                                                                     \
-        const long long lane_ = threadIdx.x & 31;                                         \
-        const long long nw_ = ((long long)gridDim.x * blockDim.x) >> 5;                   \
-        for (long long base_ = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5)  \
-                               * (32 * kU);                                               \
-             base_ < (n); base_ += nw_ * (32 * kU)) {                                     \
-            long long idx[kU];                                                            \
-            _Pragma("unroll") for (int j = 0; j < kU; ++j) idx[j] = base_ + lane_ + 32 * j;
+        const uint32_t n_ = (uint32_t)(n);                                                \
+        const uint32_t lane_ = threadIdx.x & 31u;                                         \
+        const uint32_t step_ = ((gridDim.x * blockDim.x) >> 5) * (32u * (U));             \
+        for (uint32_t base_ = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32u * (U)); \
+             base_ < n_; base_ += step_) {                                                \
+            uint32_t idx[U];                                                              \
+            _Pragma("unroll") for (int j = 0; j < (U); ++j) idx[j] = base_ + lane_ + 32u * j;
 #define WARP_STREAM_END \
         }               \
     }
@@ -306,8 +312,9 @@ __global__ void k_cgA_dir(Dev g, long long n, const uint8_t* __restrict__ ufl,
                           const T* __restrict__ rv, T* __restrict__ pv, Ctl* ctl,
                           const CgState* st) {
     count_launch(ctl);
+    constexpr int kU = StreamU<T>::v;
     const T beta = (T)(st->first ? 0.0 : st->beta);
-    WARP_STREAM_BEGIN(n)
+    WARP_STREAM_BEGIN_U(n, kU)
         int gh[kU];
         T r[kU], p[kU];
 #pragma unroll
@@ -322,16 +329,6 @@ __global__ void k_cgA_dir(Dev g, long long n, const uint8_t* __restrict__ ufl,
 // Entries per thread and step of the stencil kernels (independent gathers in flight).
 template <typename T> struct MvU { static constexpr int v = 4; };
 template <> struct MvU<double> { static constexpr int v = 2; };
-
-#define WARP_STREAM_BEGIN_U(n, U)                                                         \
-    {                                                                                     \
-        const long long lane_ = threadIdx.x & 31;                                         \
-        const long long nw_ = ((long long)gridDim.x * blockDim.x) >> 5;                   \
-        for (long long base_ = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5)  \
-                               * (32 * (U));                                              \
-             base_ < (n); base_ += nw_ * (32 * (U))) {                                    \
-            long long idx[U];                                                             \
-            _Pragma("unroll") for (int j = 0; j < (U); ++j) idx[j] = base_ + lane_ + 32 * j;
 
 // q = A' p and p.q.  The neighbour indices come from the table (coalesced rows); missing
 // neighbours point at the zero entry p[n_u].
@@ -381,9 +378,10 @@ __global__ void k_cgA_update(Dev g, long long n, const uint8_t* __restrict__ ufl
                              const T* __restrict__ qv, Ctl* ctl, CgState* st,
                              double* partials, int slot) {
     count_launch(ctl);
+    constexpr int kU = StreamU<T>::v;
     const T alpha = (T)st->alpha;
     T a0 = (T)0, a1 = (T)0;
-    WARP_STREAM_BEGIN(n)
+    WARP_STREAM_BEGIN_U(n, kU)
         int gh[kU];
         T xx[kU], p[kU], r[kU], q[kU];
 #pragma unroll
@@ -447,8 +445,9 @@ template <typename T>
 __global__ void k_cgS_dir(Dev g, long long n, const T* __restrict__ invd, const T* __restrict__ rv,
                           T* __restrict__ pv, Ctl* ctl, const CgState* st) {
     count_launch(ctl);
+    constexpr int kU = StreamU<T>::v;
     const T beta = (T)(st->first ? 0.0 : st->beta);
-    WARP_STREAM_BEGIN(n)
+    WARP_STREAM_BEGIN_U(n, kU)
         T r[kU], w[kU], p[kU];
 #pragma unroll
         for (int j = 0; j < kU; ++j)
@@ -524,9 +523,10 @@ __global__ void k_cgS_update(Dev g, long long n, const T* __restrict__ invd, T* 
                              const T* __restrict__ qv, Ctl* ctl, CgState* st,
                              double* partials, int slot) {
     count_launch(ctl);
+    constexpr int kU = StreamU<T>::v;
     const T alpha = (T)st->alpha;
     T a0 = (T)0, a1 = (T)0;
-    WARP_STREAM_BEGIN(n)
+    WARP_STREAM_BEGIN_U(n, kU)
         T xx[kU], p[kU], r[kU], q[kU], w[kU];
 #pragma unroll
         for (int j = 0; j < kU; ++j)
@@ -1021,9 +1021,34 @@ static inline dim3 tgrid(const Handle& H) {
     const long long nt = gx * gy * H.g.nz;
     return dim3((unsigned)(nt < H.target_blocks ? nt : H.target_blocks));
 }
-static inline dim3 sgrid(const Handle& H, long long n) {
+// Resident blocks of kBlock threads per SM for kernel k (cached per device and kernel).
+static int resident_blocks(const void* k) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(dev, k);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, 0) != cudaSuccess || nb < 1) {
+        (void)cudaGetLastError();
+        nb = 1;
+    }
+    cache[key] = nb;
+    return nb;
+}
+
+// Streaming grids: one block per kBlock entries, at most one wave of resident blocks
+// (nsm x min(blocks per SM of the launch shape, resident blocks of the kernel)), so
+// that the grid-stride loops end together instead of leaving a partial last wave.
+template <class K>
+static inline dim3 sgrid(const Handle& H, long long n, K k) {
     const long long nb = (n + kBlock - 1) / kBlock;
-    return dim3((unsigned)(nb < H.target_blocks ? (nb > 0 ? nb : 1) : H.target_blocks));
+    const long long cap = std::min<long long>(H.target_blocks,
+                                              (long long)H.nsm * resident_blocks((const void*)k));
+    return dim3((unsigned)std::max<long long>(1, std::min(nb, cap)));
 }
 static inline dim3 sblock() { return dim3(kBlock); }
 
@@ -1069,14 +1094,14 @@ static void record_A_solve(Handle& H, Recorder& R, InnerA<T> v, CgState* st, int
                            const double* P, double cp, double cf, const double* bvec) {
     const Compact C = compact_of(H);
     const long long nu = H.n_u;
-    R.launch("cgA_init", k_cgA_init<T>, sgrid(H, nu), sblock(), H.g, C, v.x, v.r, P, cp, cf,
+    R.launch("cgA_init", k_cgA_init<T>, sgrid(H, nu, k_cgA_init<T>), sblock(), H.g, C, v.x, v.r, P, cp, cf,
              bvec, H.dctl, st, H.partials, s);
     R.loop(s, [&H, C, v, st, s, nu](Recorder& B) {
-        B.launch("cgA_dir", k_cgA_dir<T>, sgrid(H, nu), sblock(), H.g, nu, (const uint8_t*)H.ufl,
+        B.launch("cgA_dir", k_cgA_dir<T>, sgrid(H, nu, k_cgA_dir<T>), sblock(), H.g, nu, (const uint8_t*)H.ufl,
                  (const T*)v.r, v.p, H.dctl, (const CgState*)st);
-        B.launch("cgA_matvec", k_cgA_matvec<T>, sgrid(H, nu), sblock(), H.g, C, (const T*)v.p, v.q,
+        B.launch("cgA_matvec", k_cgA_matvec<T>, sgrid(H, nu, k_cgA_matvec<T>), sblock(), H.g, C, (const T*)v.p, v.q,
                  H.dctl, st, H.partials, s);
-        B.launch("cgA_update", k_cgA_update<T>, sgrid(H, nu), sblock(), H.g, nu,
+        B.launch("cgA_update", k_cgA_update<T>, sgrid(H, nu, k_cgA_update<T>), sblock(), H.g, nu,
                  (const uint8_t*)H.ufl, v.x, v.r, (const T*)v.p, (const T*)v.q, H.dctl, st,
                  H.partials, s);
     });
@@ -1086,7 +1111,7 @@ template <typename T>
 static void record_comp_means(Handle& H, Recorder& R, const T* v, int dense) {
     const CgState* outer = &H.dctl->out;
     const Compact C = compact_of(H);
-    R.launch("comp_big", k_comp_big<T>, sgrid(H, H.n_p), sblock(), H.g, C, (const int*)H.cmpc, v,
+    R.launch("comp_big", k_comp_big<T>, sgrid(H, H.n_p, k_comp_big<T>), sblock(), H.g, C, (const int*)H.cmpc, v,
              dense, H.cmean, H.n_big, H.dctl, outer, H.partials);
     if (H.n_small > 0) {
         const long long nb = (H.n_small + 7) / 8;
@@ -1104,15 +1129,15 @@ static void record_S_solve(Handle& H, Recorder& R, InnerS<T> v, CgState* st, int
     const Compact C = compact_of(H);
     const long long np = H.n_p;
     record_comp_means<double>(H, R, H.orr, 1);
-    R.launch("cgS_init", k_cgS_init<T>, sgrid(H, np), sblock(), H.g, C, v.invd,
+    R.launch("cgS_init", k_cgS_init<T>, sgrid(H, np, k_cgS_init<T>), sblock(), H.g, C, v.invd,
              (const int*)H.cmpc, (const double*)H.cmean, H.orr, v.x, v.r, H.dctl, st,
              (const CgState*)&H.dctl->out, H.partials, s);
     R.loop(s, [&H, C, v, st, s, np](Recorder& B) {
-        B.launch("cgS_dir", k_cgS_dir<T>, sgrid(H, np), sblock(), H.g, np, v.invd, (const T*)v.r,
+        B.launch("cgS_dir", k_cgS_dir<T>, sgrid(H, np, k_cgS_dir<T>), sblock(), H.g, np, v.invd, (const T*)v.r,
                  v.p, H.dctl, (const CgState*)st);
-        B.launch("cgS_matvec", k_cgS_matvec<T>, sgrid(H, np), sblock(), H.g, C,
+        B.launch("cgS_matvec", k_cgS_matvec<T>, sgrid(H, np, k_cgS_matvec<T>), sblock(), H.g, C,
                  v.diag, (const T*)v.p, v.q, H.dctl, st, H.partials, s);
-        B.launch("cgS_update", k_cgS_update<T>, sgrid(H, np), sblock(), H.g, np, v.invd, v.x, v.r,
+        B.launch("cgS_update", k_cgS_update<T>, sgrid(H, np, k_cgS_update<T>), sblock(), H.g, np, v.invd, v.x, v.r,
                  (const T*)v.p, (const T*)v.q, H.dctl, st, H.partials, s);
     });
     record_comp_means<T>(H, R, (const T*)v.x, 0);
@@ -1138,7 +1163,7 @@ static void record_solve_fp64(Handle& H, Recorder& R, int precond) {
              (const double*)A.x, H.og, H.orr, H.op, H.od, ctl, H.partials, s_out);
     if (precond == 1) {
         record_S_solve<double>(H, R, S, inS, s_s0);
-        R.launch("outer_start", k_outer_start<double>, sgrid(H, H.n_p), sblock(), H.g, C,
+        R.launch("outer_start", k_outer_start<double>, sgrid(H, H.n_p, k_outer_start<double>), sblock(), H.g, C,
                  (const int*)H.cmpc, (const double*)H.cmean, (const double*)S.x,
                  (const double*)H.orr, H.od, ctl, H.partials, s_out);
     }
@@ -1147,15 +1172,15 @@ static void record_solve_fp64(Handle& H, Recorder& R, int precond) {
         record_A_solve<double>(H, B, A, inA, s_a, H.od, 1.0, 0.0, nullptr);
         B.launch("outer_div", k_outer_div<double>, tgrid(H), tblock(), H.g, C, (const uint8_t*)H.mask,
                  (const double*)A.x, (const double*)H.od, H.oq, ctl, H.partials, s_out);
-        B.launch("outer_update", k_outer_update, sgrid(H, H.g.ncell), sblock(), H.g, H.op, H.orr,
+        B.launch("outer_update", k_outer_update, sgrid(H, H.g.ncell, k_outer_update), sblock(), H.g, H.op, H.orr,
                  (const double*)H.od, (const double*)H.oq, ctl, H.partials, s_out);
         if (precond == 1) {
             record_S_solve<double>(H, B, S, inS, s_s);
-            B.launch("outer_dots", k_outer_dots<double>, sgrid(H, H.n_p), sblock(), H.g, C,
+            B.launch("outer_dots", k_outer_dots<double>, sgrid(H, H.n_p, k_outer_dots<double>), sblock(), H.g, C,
                      (const int*)H.cmpc, (const double*)H.cmean, (const double*)S.x,
                      (const double*)H.orr, ctl, H.partials, s_out);
         }
-        B.launch("outer_dir", k_outer_dir<double>, sgrid(H, H.g.ncell), sblock(), H.g, C,
+        B.launch("outer_dir", k_outer_dir<double>, sgrid(H, H.g.ncell, k_outer_dir<double>), sblock(), H.g, C,
                  (const int*)H.cmpc, (const double*)H.cmean, (const double*)S.x,
                  (const double*)H.orr, H.od, ctl, (const int*)&ctl->out.done);
     });
@@ -1184,7 +1209,7 @@ static void record_solve_mixed(Handle& H, Recorder& R, int precond) {
     R.loop(s_ref, [&H, C, ctl, A64, A32, S32, inA, inA32, inS32, precond, s_ref, s_s0, s_fcg, s_a,
                    s_s, s_t](Recorder& B) {
         if (precond == 1) record_S_solve<float>(H, B, S32, inS32, s_s0);
-        B.launch("fcg_start", k_fcg_start<float>, sgrid(H, H.n_p), sblock(), H.g, C,
+        B.launch("fcg_start", k_fcg_start<float>, sgrid(H, H.n_p, k_fcg_start<float>), sblock(), H.g, C,
                  (const int*)H.cmpc, (const double*)H.cmean, (const float*)S32.x,
                  (const double*)H.orr, H.od, ctl, H.partials, s_fcg);
         B.loop(s_fcg, [&H, C, ctl, A32, S32, inA32, inS32, precond, s_fcg, s_a, s_s,
@@ -1193,13 +1218,13 @@ static void record_solve_mixed(Handle& H, Recorder& R, int precond) {
             D.launch("fcg_div", k_fcg_div<float>, tgrid(H), tblock(), H.g, C, (const uint8_t*)H.mask,
                      (const float*)A32.x, (const double*)H.od, (const double*)H.orr, H.oq, ctl,
                      H.partials, s_fcg, s_ref);
-            D.launch("fcg_update", k_fcg_update, sgrid(H, H.g.ncell), sblock(), H.g, H.op, H.orr,
+            D.launch("fcg_update", k_fcg_update, sgrid(H, H.g.ncell, k_fcg_update), sblock(), H.g, H.op, H.orr,
                      (const double*)H.od, (const double*)H.oq, ctl, H.partials, s_fcg);
             if (precond == 1) record_S_solve<float>(H, D, S32, inS32, s_s);
-            D.launch("fcg_dots", k_fcg_dots<float>, sgrid(H, H.n_p), sblock(), H.g, C,
+            D.launch("fcg_dots", k_fcg_dots<float>, sgrid(H, H.n_p, k_fcg_dots<float>), sblock(), H.g, C,
                      (const int*)H.cmpc, (const double*)H.cmean, (const float*)S32.x,
                      (const double*)H.orr, (const double*)H.oq, ctl, H.partials);
-            D.launch("fcg_dir", k_outer_dir<float>, sgrid(H, H.g.ncell), sblock(), H.g, C,
+            D.launch("fcg_dir", k_outer_dir<float>, sgrid(H, H.g.ncell, k_outer_dir<float>), sblock(), H.g, C,
                      (const int*)H.cmpc, (const double*)H.cmean, (const float*)S32.x,
                      (const double*)H.orr, H.od, ctl, (const int*)&ctl->out.skip_next);
         });
@@ -1219,7 +1244,7 @@ void record_recover(Handle& H, Recorder& R) {
     Ctl* ctl = H.dctl;
     const int s = R.new_slot();
     record_A_solve<double>(H, R, innerA64(H), &ctl->rec, s, H.op, -1.0, 1.0, nullptr);
-    R.launch("copy_u", k_copy_u, sgrid(H, H.n_u), sblock(), H.g, compact_of(H),
+    R.launch("copy_u", k_copy_u, sgrid(H, H.n_u, k_copy_u), sblock(), H.g, compact_of(H),
              (const double*)H.ax, H.u, ctl, H.partials);
 }
 
@@ -1251,23 +1276,27 @@ cudaError_t time_kernel(Handle& H, int which, int slot, float* ms) {
     const Compact C = compact_of(H);
     cudaError_t e = cudaEventRecord(H.ev0, H.stream);
     if (e != cudaSuccess) return e;
-    const dim3 gu = sgrid(H, nu), gp = sgrid(H, np), b = sblock();
+    const dim3 b = sblock();
+#define GU(k) sgrid(H, nu, k)
+#define GP(k) sgrid(H, np, k)
     cudaStream_t s = H.stream;
     switch (which) {
-        case 0: k_cgA_dir<double><<<gu, b, 0, s>>>(H.g, nu, H.ufl, H.ar, H.ap, ctl, st); break;
-        case 1: k_cgA_matvec<double><<<gu, b, 0, s>>>(H.g, C, H.ap, H.aq, ctl, st, H.partials, slot); break;
-        case 2: k_cgA_update<double><<<gu, b, 0, s>>>(H.g, nu, H.ufl, H.ax, H.ar, H.ap, H.aq, ctl, st, H.partials, slot); break;
-        case 3: k_cgS_dir<double><<<gp, b, 0, s>>>(H.g, np, H.invdSc, H.sr, H.sp, ctl, st); break;
-        case 4: k_cgS_matvec<double><<<gp, b, 0, s>>>(H.g, C, H.dSc, H.sp, H.sq, ctl, st, H.partials, slot); break;
-        case 5: k_cgS_update<double><<<gp, b, 0, s>>>(H.g, np, H.invdSc, H.sx, H.sr, H.sp, H.sq, ctl, st, H.partials, slot); break;
-        case 6: k_cgA_dir<float><<<gu, b, 0, s>>>(H.g, nu, H.ufl, H.arf, H.apf, ctl, st); break;
-        case 7: k_cgA_matvec<float><<<gu, b, 0, s>>>(H.g, C, H.apf, H.aqf, ctl, st, H.partials, slot); break;
-        case 8: k_cgA_update<float><<<gu, b, 0, s>>>(H.g, nu, H.ufl, H.axf, H.arf, H.apf, H.aqf, ctl, st, H.partials, slot); break;
-        case 9: k_cgS_dir<float><<<gp, b, 0, s>>>(H.g, np, H.invdSf, H.srf, H.spf, ctl, st); break;
-        case 10: k_cgS_matvec<float><<<gp, b, 0, s>>>(H.g, C, (const float*)nullptr, H.spf, H.sqf, ctl, st, H.partials, slot); break;
-        case 11: k_cgS_update<float><<<gp, b, 0, s>>>(H.g, np, H.invdSf, H.sxf, H.srf, H.spf, H.sqf, ctl, st, H.partials, slot); break;
+        case 0: k_cgA_dir<double><<<GU(k_cgA_dir<double>), b, 0, s>>>(H.g, nu, H.ufl, H.ar, H.ap, ctl, st); break;
+        case 1: k_cgA_matvec<double><<<GU(k_cgA_matvec<double>), b, 0, s>>>(H.g, C, H.ap, H.aq, ctl, st, H.partials, slot); break;
+        case 2: k_cgA_update<double><<<GU(k_cgA_update<double>), b, 0, s>>>(H.g, nu, H.ufl, H.ax, H.ar, H.ap, H.aq, ctl, st, H.partials, slot); break;
+        case 3: k_cgS_dir<double><<<GP(k_cgS_dir<double>), b, 0, s>>>(H.g, np, H.invdSc, H.sr, H.sp, ctl, st); break;
+        case 4: k_cgS_matvec<double><<<GP(k_cgS_matvec<double>), b, 0, s>>>(H.g, C, H.dSc, H.sp, H.sq, ctl, st, H.partials, slot); break;
+        case 5: k_cgS_update<double><<<GP(k_cgS_update<double>), b, 0, s>>>(H.g, np, H.invdSc, H.sx, H.sr, H.sp, H.sq, ctl, st, H.partials, slot); break;
+        case 6: k_cgA_dir<float><<<GU(k_cgA_dir<float>), b, 0, s>>>(H.g, nu, H.ufl, H.arf, H.apf, ctl, st); break;
+        case 7: k_cgA_matvec<float><<<GU(k_cgA_matvec<float>), b, 0, s>>>(H.g, C, H.apf, H.aqf, ctl, st, H.partials, slot); break;
+        case 8: k_cgA_update<float><<<GU(k_cgA_update<float>), b, 0, s>>>(H.g, nu, H.ufl, H.axf, H.arf, H.apf, H.aqf, ctl, st, H.partials, slot); break;
+        case 9: k_cgS_dir<float><<<GP(k_cgS_dir<float>), b, 0, s>>>(H.g, np, H.invdSf, H.srf, H.spf, ctl, st); break;
+        case 10: k_cgS_matvec<float><<<GP(k_cgS_matvec<float>), b, 0, s>>>(H.g, C, (const float*)nullptr, H.spf, H.sqf, ctl, st, H.partials, slot); break;
+        case 11: k_cgS_update<float><<<GP(k_cgS_update<float>), b, 0, s>>>(H.g, np, H.invdSf, H.sxf, H.srf, H.spf, H.sqf, ctl, st, H.partials, slot); break;
         default: return cudaErrorInvalidValue;
     }
+#undef GU
+#undef GP
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventRecord(H.ev1, H.stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(H.ev1);
@@ -1278,10 +1307,10 @@ cudaError_t time_kernel(Handle& H, int which, int slot, float* ms) {
 cudaError_t launch_build_tables(Handle& H) {
     const Compact C = compact_of(H);
     if (H.n_u > 0)
-        k_build_nbA<<<sgrid(H, H.n_u), sblock(), 0, H.stream>>>(H.g, C, H.nbA);
+        k_build_nbA<<<sgrid(H, H.n_u, k_build_nbA), sblock(), 0, H.stream>>>(H.g, C, H.nbA);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || H.n_p == 0) return e;
-    k_build_nbS<<<sgrid(H, H.n_p), sblock(), 0, H.stream>>>(H.g, C, H.flags, H.nbS, H.codeS, H.dSc);
+    k_build_nbS<<<sgrid(H, H.n_p, k_build_nbS), sblock(), 0, H.stream>>>(H.g, C, H.flags, H.nbS, H.codeS, H.dSc);
     return cudaGetLastError();
 }
 
