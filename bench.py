@@ -7,13 +7,14 @@ on "spheres128" (128^3 periodic overlapping spheres, radii U[4,8), porosity 0.40
 f = e_x).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--patterns mixed,batch,serve|none]
+                    [--patterns mixed,batch,serve,tight|none]
 
 Prints one JSON line.  value = Schur solves per second with the mask resident on the
 device; e2e = the same with the mask in host memory (H2D copy and permeability D2H inside
 the timed region).  After the timed region (N = 1 only) the line also reports the
 mixed-precision solves of the same workload, a batch of 64 uneven packings solved by one
-graph launch, and a Poisson-arrival serving run with p50/p99 latency.  --impl reference
+graph launch, a Poisson-arrival serving run with p50/p99 latency, and the tight 256^3
+packing (porosity 0.15) in mixed precision against FP64.  --impl reference
 times the FP64 CPU oracle on a bounded sample of the same workload and scales it to whole
 solves with the oracle's own recorded iteration counts.
 """
@@ -41,25 +42,52 @@ DESC = ("spheres128: 128^3 periodic overlapping solid spheres, radii U[4,8), por
         "(unpreconditioned), inner Jacobi-PCG to 1e-12")
 
 
-# Per hot kernel: algorithmic bytes and FP64/FP32 FLOPs for n_u unknown faces and n_p
-# fluid cells (w = 8 or 4 bytes; 4-byte work-list entry and 1 flag byte per unknown;
-# the SIMPLE stencil touches 2 n_u open faces, 3 FLOP each).
+# Per hot kernel and entry (unknown face for cgA_*, fluid cell for cgS_*): algorithmic
+# bytes of the compact layout and FP64 pipe lane-operations (DFMA, DADD and DMUL count
+# one each; the pipe retires 2 per clock and SM).  w = 8 (FP64) or 4 (FP32) bytes per
+# value; neighbour tables hold 2d 4-byte indices per entry, stencil neighbours are taken
+# as cache hits (each value is read from DRAM once per launch).
+#   cgA_dir     p = w_g r + beta p            read r, p, flag; write p          2 ops
+#   cgA_matvec  q = diag_g p - sum p_nb, p.q  read table, flag, p; write q      7 ops
+#   cgA_update  x, r, r.z, z.z                read x, p, r, q, flag; write x, r 5 ops
+#   cgS_dir     p = invd r + beta p           read r, invd, p; write p          2 ops
+#   cgS_matvec  q = dS p - sum w p_nb, p.q    read table, code, p (, dS); write q 8 ops
+#   cgS_update  x, r, r.z, z.z                read x, p, r, q, invd; write x, r 5 ops
 def kernel_model(name, nu, npf, d):
     w = 4 if name.endswith("_f32") else 8
     base = name.replace("_f32", "")
+    nb = 2 * d * 4
     bytes_ = {
-        "cgA_dir": (3 * w + 1 + 4) * nu,
-        "cgA_matvec": (2 * w + 1 + 4) * nu,
-        "cgA_update": (6 * w + 1 + 4) * nu,
-        "cgS_dir": (4 * w + 4) * npf,
-        "cgS_matvec": (2 * w + 4) * npf + 2 * nu,
-        "cgS_update": (7 * w + 4) * npf,
+        "cgA_dir": (3 * w + 1) * nu,
+        "cgA_matvec": (nb + 1 + 2 * w) * nu,
+        "cgA_update": (6 * w + 1) * nu,
+        "cgS_dir": 4 * w * npf,
+        "cgS_matvec": (nb + 4 + 2 * w + (w if w == 8 else 0)) * npf,
+        "cgS_update": 7 * w * npf,
     }[base]
-    flops = {
-        "cgA_dir": 3 * nu, "cgA_matvec": 9 * nu, "cgA_update": 9 * nu,
-        "cgS_dir": 3 * npf, "cgS_matvec": 6 * nu + 2 * npf, "cgS_update": 9 * npf,
+    ops = {
+        "cgA_dir": 2 * nu, "cgA_matvec": 7 * nu, "cgA_update": 5 * nu,
+        "cgS_dir": 2 * npf, "cgS_matvec": 8 * npf, "cgS_update": 5 * npf,
     }[base]
-    return bytes_, flops, w
+    return bytes_, ops, w
+
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, bytes) of the
+# hot kernels on this workload from one ncu capture (cold cache) of the kernel sources
+# whose SHA-256 is given; reported as null once the sources differ.
+NCU_TRAFFIC = {
+    "sources_sha256": "a91de65beb8e2857ce05a5be40727db145f17857e282eacded912c8b24b56103",
+    "bytes": {"cgA_dir": 38441984, "cgA_matvec": 77139968, "cgA_update": 75935744, "cgS_dir": 20133632, "cgS_matvec": 36966912, "cgS_update": 33583104, "cgA_dir_f32": 20353536, "cgA_matvec_f32": 66861568, "cgA_update_f32": 38469888, "cgS_dir_f32": 10069248, "cgS_matvec_f32": 26868480, "cgS_update_f32": 16808448},
+}
+
+
+def kernel_sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in ("paper_2307_05266_gb300/csrc/krylov.cu", "paper_2307_05266_gb300/csrc/common.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def make_mask(rank: int = 0):
@@ -272,13 +300,67 @@ def serve_specs(n_req, max_edge, seed=7):
     return specs, axes, rng
 
 
+def time_kernels(binding, torch, mask_dev, reps):
+    """Per-kernel timing on the headline workload: CUDA events around single launches on
+    the geometry's stream, L2 flushed before every launch by reading a 512 MiB buffer
+    (clean lines, so the timed kernel pays no write-back of the flush), mean over reps - 2
+    launches; the FP32 kernels run on the buffers of a mixed-precision solve."""
+    w = WORKLOAD
+    peak_bw, sm_mhz, _ = load_peaks()
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    fp64_peak = nsm * 2 * sm_mhz * 1e6 / 1e12
+    g = binding.Geometry(mask_dev)
+    g.set_force(w["force"])
+    g.solve(precond=binding.SIMPLE, precision=binding.MIXED, tol=w["tol"])
+    info = g.info
+    nu = int(sum(info.n_unknown[a] for a in range(info.ndim)))
+    npf = int(info.n_fluid)
+    flush = torch.ones(64 * 1024 * 1024, dtype=torch.float64, device="cuda")
+    sink = torch.empty((), dtype=torch.float64, device="cuda")
+    traffic_ok = NCU_TRAFFIC["sources_sha256"] == kernel_sources_sha()
+    kern = {}
+    for name in binding.KERNELS:
+        times = []
+        for _ in range(reps):
+            torch.sum(flush, 0, out=sink)
+            times.append(g.time_kernel(name))
+        avg = statistics.mean(times[2:]) if reps > 2 else statistics.mean(times)
+        b, ops, wb = kernel_model(name, nu, npf, info.ndim)
+        gbps = b / (avg / 1e3) / 1e9
+        tops = ops / (avg / 1e3) / 1e12
+        f_hbm, f_alu = gbps / peak_bw, (tops / fp64_peak if wb == 8 else 0.0)
+        tr = NCU_TRAFFIC["bytes"].get(name) if traffic_ok else None
+        kern[name] = {"ms": avg, "alg_bytes": b, "alg_GBps": gbps,
+                      "fp64_lane_ops": ops if wb == 8 else 0,
+                      "fp64_Tops": tops if wb == 8 else 0.0, "frac_hbm": f_hbm,
+                      "frac_fp64_pipe": f_alu, "ncu_dram_bytes": tr,
+                      "bound": "alu" if f_alu > f_hbm else "hbm"}
+    g.close()
+    del flush
+    return kern, nu, npf
+
+
+def kernels_only(args):
+    """One launch (or --steps launches) of each hot kernel on the headline workload, for
+    profiling the kernels alone; prints the per-kernel timing as one JSON line."""
+    import torch
+
+    from paper_2307_05266_gb300 import binding
+    torch.cuda.set_device(0)
+    binding.load()
+    mask_dev = torch.from_numpy(make_mask(0)).cuda()
+    kern, nu, npf = time_kernels(binding, torch, mask_dev, max(1, args.steps))
+    print(json.dumps({"workload": DESC, "n_unknown": nu, "n_fluid": npf, "kernels": kern}))
+    return 0
+
+
 def gpu_arm(args):
     patterns = set() if args.patterns == "none" else set(args.patterns.split(","))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     pool = pending = None
-    if world == 1 and (patterns & {"batch", "serve"}):
+    if world == 1 and (patterns & {"batch", "serve", "tight"}):
         # masks of the extra patterns are generated by spawned workers (started before
         # any GPU call) while the headline runs
         import multiprocessing as mp
@@ -287,7 +369,9 @@ def gpu_arm(args):
         sspecs, saxes, srng = serve_specs(args.serve_requests, args.serve_max_edge)
         if "serve" not in patterns:
             sspecs = []
-        pending = (pool.map_async(_gen, bspecs), pool.map_async(_gen, sspecs))
+        tspecs = [TIGHT] if "tight" in patterns else []
+        pending = (pool.map_async(_gen, bspecs), pool.map_async(_gen, sspecs),
+                   pool.map_async(_gen, tspecs))
 
     import torch
     import torch.distributed as dist
@@ -310,7 +394,8 @@ def gpu_arm(args):
     porosity = float(mask_np.mean())
     stream = torch.cuda.current_stream()
     precs = (("uzawa", binding.UZAWA), ("simple", binding.SIMPLE))
-    solve_kw = dict(tol=w["tol"], tol_inner_A=w["tol_inner"], tol_inner_S=w["tol_inner"])
+    solve_kw = dict(tol=w["tol"], tol_inner_A=w["tol_inner"], tol_inner_S=w["tol_inner"],
+                    loop_mode=binding.LOOP_HOST if args.loop == "host" else binding.LOOP_GRAPH)
 
     def step(mask, rec):
         g = binding.Geometry(mask)
@@ -378,34 +463,10 @@ def gpu_arm(args):
                      "inner_S": rows[-1]["inner_S"], "recovery": rows[-1]["recovery"],
                      "k": rows[-1]["k"], "rel_res": rows[-1]["rel_res"]}
 
-    # per-kernel timing: CUDA events around single launches on the bench stream, L2
-    # flushed (a 512 MiB write) before every launch; FP32 kernels after a mixed solve
     peak_bw, sm_mhz, peak_kind = load_peaks()
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
-    fp64_peak = nsm * 2 * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s: 2 DFMA/clk/SM, 2 FLOP each
-    g = binding.Geometry(mask_dev)
-    g.set_force(w["force"])
-    g.solve(precond=binding.SIMPLE, precision=binding.MIXED, tol=w["tol"])
-    info = g.info
-    nu = int(sum(info.n_unknown[a] for a in range(info.ndim)))
-    npf = int(info.n_fluid)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device="cuda")
-    kern = {}
-    for name in binding.KERNELS:
-        times = []
-        for _ in range(12):
-            flush.zero_()
-            times.append(g.time_kernel(name))
-        avg = statistics.mean(times[2:])
-        b, fl, wb = kernel_model(name, nu, npf, info.ndim)
-        gbps = b / (avg / 1e3) / 1e9
-        tflops = fl / (avg / 1e3) / 1e12
-        f_hbm, f_alu = gbps / peak_bw, (tflops / fp64_peak if wb == 8 else 0.0)
-        kern[name] = {"ms": avg, "alg_bytes": b, "alg_GBps": gbps, "fp64_flop": fl if wb == 8 else 0,
-                      "TFLOPs": tflops, "frac_hbm": f_hbm, "frac_fp64": f_alu,
-                      "bound": "alu" if f_alu > f_hbm else "hbm"}
-    g.close()
-    del flush
+    fp64_peak = nsm * 2 * sm_mhz * 1e6 / 1e12   # T lane-ops/s: 2 FP64 lanes per clock and SM
+    kern, nu, npf = time_kernels(binding, torch, mask_dev, 12)
     # time share of each FP64 kernel in one headline step (launch counts from iterations)
     launches_of = {"A": sum(per[p]["inner_A"] + per[p]["recovery"] for p in per),
                    "S": sum(per[p]["inner_S"] for p in per)}
@@ -419,13 +480,15 @@ def gpu_arm(args):
     def roof_of(name):
         kk = kern[name]
         if kk["bound"] == "alu":
-            return {"bound": "alu", "kernel": name, "achieved": kk["TFLOPs"], "peak": fp64_peak,
-                    "unit": "TFLOP/s", "frac": kk["frac_fp64"], "traffic": None,
-                    "peak_kind": f"derived FP64 peak: {nsm} SMs x 2 DFMA/clk x 2 FLOP x "
-                                 f"{sm_mhz:.0f} MHz"}
+            return {"bound": "alu", "kernel": name, "achieved": kk["fp64_Tops"],
+                    "peak": fp64_peak, "unit": "T FP64 lane-ops/s", "frac": kk["frac_fp64_pipe"],
+                    "traffic": kk["ncu_dram_bytes"], "alg_bytes": kk["alg_bytes"],
+                    "peak_kind": f"derived FP64 pipe peak: {nsm} SMs x 2 lanes/clk x "
+                                 f"{sm_mhz:.0f} MHz (DFMA, DADD, DMUL one lane-op each)"}
         return {"bound": "hbm", "kernel": name, "achieved": kk["alg_GBps"], "peak": peak_bw,
-                "unit": "GB/s", "frac": kk["frac_hbm"], "traffic": None,
-                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+                "unit": "GB/s", "frac": kk["frac_hbm"], "traffic": kk["ncu_dram_bytes"],
+                "alg_bytes": kk["alg_bytes"],
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)"}
 
     roof = roof_of(dom)
     roof["timing"] = ("CUDA events around single launches on the bench stream after the timed "
@@ -458,12 +521,14 @@ def gpu_arm(args):
     if world == 1 and "mixed" in patterns:
         line["mixed_precision"] = mixed_pattern(binding, mask_dev, per, solve_kw)
     if pending is not None:
-        bmasks, smasks = pending[0].get(), pending[1].get()
+        bmasks, smasks, tmasks = pending[0].get(), pending[1].get(), pending[2].get()
         pool.close()
         if "batch" in patterns:
             line["batched"] = batch_pattern(binding, torch, bmasks, stream)
         if "serve" in patterns:
             line["serving"] = serve_pattern(binding, torch, smasks, saxes, srng, args)
+        if "tight" in patterns:
+            line["tight256"] = tight_pattern(binding, torch, tmasks[0])
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -591,6 +656,43 @@ def serve_pattern(binding, torch, masks, axes, rng, args):
             "latency_s": lat}
 
 
+# Tight geometry: 256^3, porosity 0.15, radii U[2, 4) (high surface-to-volume ratio).
+TIGHT = (256, 2.0, 4.0, 0.15, 0)
+
+
+def tight_pattern(binding, torch, mask):
+    """Mixed-precision SIMPLE and Uzawa solves of the tight 256^3 packing against the FP64
+    SIMPLE solve of the same geometry on the GPU (the FP64 path is the one checked
+    against the oracle; a whole oracle solve of this size does not fit the bench)."""
+    out = {"grid": 256, "porosity": float(mask.mean()), "r": [TIGHT[1], TIGHT[2]],
+           "seed": TIGHT[4]}
+    g = binding.Geometry(torch.from_numpy(mask).cuda())
+    g.set_force(WORKLOAD["force"])
+    info = g.info
+    out["n_unknown"] = int(sum(info.n_unknown[a] for a in range(info.ndim)))
+    out["n_fluid"] = int(info.n_fluid)
+    runs = (("fp64_simple", binding.SIMPLE, binding.FP64),
+            ("mixed_simple", binding.SIMPLE, binding.MIXED),
+            ("mixed_uzawa", binding.UZAWA, binding.MIXED))
+    for name, pc, prec in runs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = g.solve(precond=pc, precision=prec, tol=1e-8, max_outer=20000, allow_fail=True)
+        g.recover_velocity(allow_fail=True)
+        k = g.permeability(0)
+        dt = time.perf_counter() - t0
+        out[name] = {"s": dt, "status": st.status, "outer": st.outer_iters,
+                     "inner_A_f64": st.inner_iters_A, "inner_S_f64": st.inner_iters_S,
+                     "inner_A_f32": st.inner_iters_A_f32, "inner_S_f32": st.inner_iters_S_f32,
+                     "refinements": st.refinements, "k": k}
+    g.close()
+    k64 = out["fp64_simple"]["k"]
+    for name in ("mixed_simple", "mixed_uzawa"):
+        out[name]["k_rel_err_vs_gpu_fp64"] = abs(out[name]["k"] - k64) / abs(k64)
+        out[name]["speedup_vs_fp64_simple"] = out["fp64_simple"]["s"] / out[name]["s"]
+    return out
+
+
 import numpy as np  # noqa: E402  (used by the patterns)
 
 
@@ -600,14 +702,21 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--patterns", default="mixed,batch,serve")
+    ap.add_argument("--patterns", default="mixed,batch,serve,tight")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-max-edge", type=int, default=192)
+    ap.add_argument("--loop", default="graph", choices=["graph", "host"],
+                    help="host: loops driven from the host, one plain launch per kernel (for "
+                         "profilers that cannot see kernel nodes under conditional nodes)")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="time one launch per --steps of each hot kernel and exit (profiling)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample:
         print(json.dumps(oracle_sample()))
         return 0
+    if args.kernels_only:
+        return kernels_only(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
