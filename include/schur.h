@@ -185,8 +185,14 @@ int schur_solve_A(schur_geom_t g, const double* b, double* x, double tol, int ma
 /* Profiling hook: one launch of a hot solver kernel on the handle's stream, bracketed by
  * two CUDA events; *ms receives the elapsed time.  kernel: 0 inner-A direction update,
  * 1 inner-A stencil A p (with p.q), 2 inner-A x/r update (with r.z, z.z), 3-5 the same
- * three for the SIMPLE operator, 6-11 the FP32 versions of 0-5 (after a mixed solve).  The kernel works on the solver's own buffers (their
- * contents after the last call); results of later calls are unaffected.  Synchronises. */
+ * three for the SIMPLE operator, 6-11 the FP32 versions of 0-5 (after a mixed solve);
+ * 12 the persistent inner-A CG kernel that the solver launches (one cooperative launch
+ * running SCHUR_TIMED_LOOP_ITERS iterations of all three phases on a fixed right-hand
+ * side), 13 the same for the SIMPLE operator, 14-15 their FP32 versions.  Ids 0-11 time
+ * the phases one launch each (the solver itself runs them inside 12-15).  The kernel
+ * works on the solver's own buffers (their contents after the last call); results of
+ * later calls are unaffected.  Synchronises. */
+#define SCHUR_TIMED_LOOP_ITERS 20
 int schur_time_kernel(schur_geom_t g, int kernel, float* ms);
 
 /* Allocation-free Darcy permeability of a caller-owned velocity field (no counterpart in

@@ -36,7 +36,10 @@ EXPORTED = [
 ]
 KERNELS = {"cgA_dir": 0, "cgA_matvec": 1, "cgA_update": 2, "cgS_dir": 3, "cgS_matvec": 4,
            "cgS_update": 5, "cgA_dir_f32": 6, "cgA_matvec_f32": 7, "cgA_update_f32": 8,
-           "cgS_dir_f32": 9, "cgS_matvec_f32": 10, "cgS_update_f32": 11}
+           "cgS_dir_f32": 9, "cgS_matvec_f32": 10, "cgS_update_f32": 11,
+           "cgA_loop": 12, "cgS_loop": 13, "cgA_loop_f32": 14, "cgS_loop_f32": 15}
+# iterations of one timed launch of the persistent loop kernels (ids 12-15)
+TIMED_LOOP_ITERS = 20
 
 
 class Opts(C.Structure):

@@ -271,6 +271,8 @@ void reset_call(Handle& H, int use_graph) {
     c->f[2] = H.force[2];
     c->launches = 0;
     c->inner_status = 0;
+    c->bar_count = 0;
+    c->bar_err = 0;
     c->ticket = 0;
     c->inA.total = c->inS.total = c->out.total = c->solo.total = c->rec.total = 0;
     c->inA32.total = c->inS32.total = 0;
@@ -289,9 +291,25 @@ int download(Handle& H) {
     return SCHUR_OK;
 }
 
+// Status of a finished call: a failed grid barrier in any inner solve (ctl->bar_err)
+// overrides the Krylov statuses, whose values are then meaningless.
+int map_status(int st);
+
+int call_status(const Ctl* c, int st) {
+    if (c->bar_err) return SCHUR_ECUDA;
+    return map_status(st);
+}
+
+const char* status_text(const Handle& H, const char* otherwise) {
+    return H.hctl->bar_err ? "an inner-solve grid barrier wait ran past its limit (blocks of a "
+                             "cooperative launch were not co-resident)"
+                           : otherwise;
+}
+
 int map_status(int st) {
     if (st == ST_OK) return SCHUR_OK;
     if (st == ST_BREAKDOWN) return SCHUR_EBREAKDOWN;
+    if (st == ST_BARRIER) return SCHUR_ECUDA;
     return SCHUR_ENOTCONV;
 }
 
@@ -375,7 +393,7 @@ int download_ctl_async(Handle& H) {
 void fill_solve_stats(Handle& H, int precision, schur_stats* stats) {
     const Ctl* c = H.hctl;
     std::memset(stats, 0, sizeof(*stats));
-    stats->status = map_status(c->out.status);
+    stats->status = call_status(c, c->out.status);
     stats->outer_iters = c->out.iter;
     stats->zero_rhs = c->zero_rhs;
     stats->inner_status = map_status(c->inner_status);
@@ -393,7 +411,7 @@ void fill_solve_stats(Handle& H, int precision, schur_stats* stats) {
 void fill_recover_stats(Handle& H, schur_stats* stats) {
     const Ctl* c = H.hctl;
     std::memset(stats, 0, sizeof(*stats));
-    stats->status = map_status(c->rec.status);
+    stats->status = call_status(c, c->rec.status);
     stats->inner_status = map_status(c->inner_status);
     stats->inner_iters_A = c->rec.total;
     stats->rel_res = c->rec.rel;
@@ -581,8 +599,8 @@ int schur_solve(schur_geom_t G, const schur_opts* opts, schur_stats* stats) {
     H.solved = true;
     H.recovered = false;
     if (stats) fill_solve_stats(H, o.precision, stats);
-    const int st = map_status(H.hctl->out.status);
-    if (st != SCHUR_OK) set_error(st, "outer iteration did not converge");
+    const int st = call_status(H.hctl, H.hctl->out.status);
+    if (st != SCHUR_OK) set_error(st, status_text(H, "outer iteration did not converge"));
     return st;
 }
 
@@ -609,8 +627,8 @@ int schur_recover_velocity(schur_geom_t G, schur_stats* stats) {
     if ((rc = download(H))) return rc;
     H.recovered = true;
     if (stats) fill_recover_stats(H, stats);
-    const int st = map_status(H.hctl->rec.status);
-    if (st != SCHUR_OK) set_error(st, "velocity recovery did not converge");
+    const int st = call_status(H.hctl, H.hctl->rec.status);
+    if (st != SCHUR_OK) set_error(st, status_text(H, "velocity recovery did not converge"));
     return st;
 }
 
@@ -659,9 +677,9 @@ int schur_finish(schur_geom_t G, schur_stats* solve_stats, schur_stats* recover_
     H.solved = H.recovered = true;
     if (solve_stats) fill_solve_stats(H, H.pending_precision, solve_stats);
     if (recover_stats) fill_recover_stats(H, recover_stats);
-    int st = map_status(H.hctl->out.status);
-    if (st == SCHUR_OK) st = map_status(H.hctl->rec.status);
-    if (st != SCHUR_OK) set_error(st, "solve or recovery did not converge");
+    int st = call_status(H.hctl, H.hctl->out.status);
+    if (st == SCHUR_OK) st = call_status(H.hctl, H.hctl->rec.status);
+    if (st != SCHUR_OK) set_error(st, status_text(H, "solve or recovery did not converge"));
     return st;
 }
 
@@ -764,15 +782,15 @@ int schur_solve_A(schur_geom_t G, const double* b, double* x, double tol, int ma
     CUDA_TRY(launch_scatter_f64(H, H.ax, H.ulist, x, H.n_u), "scatter solution");
     if ((rc = download(H))) return rc;
     if (iters) *iters = c->solo.iter;
-    const int st = map_status(c->solo.status);
-    if (st != SCHUR_OK) set_error(st, "inner A solve did not converge");
+    const int st = call_status(c, c->solo.status);
+    if (st != SCHUR_OK) set_error(st, status_text(H, "inner A solve did not converge"));
     return st;
 }
 
 int schur_time_kernel(schur_geom_t G, int kernel, float* ms) {
     if (!G || !ms) return set_error(SCHUR_EINVAL, "null argument");
-    if (kernel < 0 || kernel > 11) return set_error(SCHUR_EINVAL, "kernel id must be 0..11");
-    if (kernel > 5 && !G->H.axf)
+    if (kernel < 0 || kernel > 15) return set_error(SCHUR_EINVAL, "kernel id must be 0..15");
+    if (((kernel > 5 && kernel < 12) || kernel > 13) && !G->H.axf)
         return set_error(SCHUR_ESTATE, "FP32 kernels need a mixed-precision solve first");
     Handle& H = G->H;
     reset_call(H, 0);  // no graph: the condition slot is only written to device memory

@@ -28,7 +28,7 @@ constexpr double kZeroRhsRtol = 1e-12; // g == 0 when ||g|| <= this * || |B| |u|
 constexpr int kMaxBig = 8;             // fluid components reduced by the full grid
 constexpr long long kBigMin = 2048;    // smallest component treated as "big"
 
-enum Status : int { ST_OK = 0, ST_NOTCONV = 3, ST_BREAKDOWN = 4 };
+enum Status : int { ST_OK = 0, ST_NOTCONV = 3, ST_BREAKDOWN = 4, ST_BARRIER = 5 };
 
 struct Dev {
     int nx, ny, nz, d;
@@ -114,6 +114,10 @@ struct Ctl {
     long long launches;
     unsigned int ticket;
     unsigned int pad1;
+    // grid barrier of the cooperative inner-solve kernels: arrivals, and a sticky flag set
+    // when a wait ran past its limit
+    unsigned int bar_count;
+    unsigned int bar_err;
 };
 
 inline long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
@@ -220,6 +224,50 @@ __device__ __forceinline__ bool reduce_last_block(double (&v)[K], double* partia
     return true;
 }
 
+// ---- grid barrier of a cooperative launch ------------------------------------------
+
+// Polls of one barrier wait before it gives up: the first kBarrierBusy polls spin, the
+// rest sleep >= 128 ns each, so the limit is well over half a second, far beyond any
+// legal wait (microseconds).
+constexpr unsigned kBarrierSpins = 1u << 22;
+constexpr unsigned kBarrierBusy = 1u << 10;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// All blocks of the grid meet here (the launch is cooperative, so they are co-resident).
+// ctl->bar_count counts arrivals and is zeroed before the launch; `target` is this
+// block's running count of expected arrivals.  A wait that exceeds kBarrierSpins polls,
+// or that sees another block's failure, sets ctl->bar_err and returns false, and the
+// caller leaves its loop: the kernel then ends with an error status instead of hanging.
+__device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned& target) {
+    __shared__ unsigned s_ok;
+    __syncthreads();
+    target += gridDim.x;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(&ctl->bar_count, 1u);
+        unsigned ok = 1u;
+        for (unsigned spin = 0;; ++spin) {
+            if ((int)(ld_acquire_u32(&ctl->bar_count) - target) >= 0) break;
+            if (ld_acquire_u32(&ctl->bar_err) != 0u) { ok = 0u; break; }
+            if (spin >= kBarrierSpins) {
+                atomicExch(&ctl->bar_err, 1u);
+                ok = 0u;
+                break;
+            }
+            if (spin >= kBarrierBusy) __nanosleep(128);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0u;
+}
+
 // ---- launch recorder: direct launches on a stream, or nodes of a CUDA graph -------
 
 template <class T> struct ident { using type = T; };
@@ -264,6 +312,33 @@ class Recorder {
         cudaGraphNode_t node;
         check(cudaGraphAddKernelNode(&node, graph_, have_last_ ? &last_ : nullptr,
                                      have_last_ ? 1 : 0, &p), name);
+        last_ = node;
+        have_last_ = true;
+    }
+
+    // A cooperative launch (all blocks co-resident; the kernel may use grid_barrier).
+    template <typename... P>
+    void launch_coop(const char* name, void (*k)(P...), dim3 grid, dim3 block,
+                     typename ident<P>::type... args) {
+        if (!ok()) return;
+        void* ptrs[sizeof...(P) + 1] = {(void*)&args...};
+        if (!graph_) {
+            check(cudaLaunchCooperativeKernel((const void*)k, grid, block, ptrs, 0, stream_), name);
+            return;
+        }
+        cudaKernelNodeParams p = {};
+        p.func = (void*)k;
+        p.gridDim = grid;
+        p.blockDim = block;
+        p.sharedMemBytes = 0;
+        p.kernelParams = ptrs;
+        cudaGraphNode_t node;
+        check(cudaGraphAddKernelNode(&node, graph_, have_last_ ? &last_ : nullptr,
+                                     have_last_ ? 1 : 0, &p), name);
+        if (!ok()) return;
+        cudaLaunchAttributeValue v = {};
+        v.cooperative = 1;
+        check(cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributeCooperative, &v), name);
         last_ = node;
         have_last_ = true;
     }

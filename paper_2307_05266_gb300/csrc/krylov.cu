@@ -2,11 +2,17 @@
 //
 // Inner solves: Jacobi-preconditioned CG from x_0 = 0 with the stopping rule of
 // Section 3.2, ||M^-1 r_k|| / ||M^-1 r_0|| < eps, for A (face space, M = diag(A)) and
-// for S-hat_simple (cell space, M = diag(S-hat)).  One CG iteration is three kernels:
+// for S-hat_simple (cell space, M = diag(S-hat)).  One CG iteration has three phases:
 //   dir:    p = z + beta p  (z = M^-1 r formed on the fly; beta = 0 on the first pass)
-//   matvec: q = Op p and the partial sums of p.q; the last block forms alpha = rho/p.q
-//   update: x += alpha p, r -= alpha q, partial sums of r.z and z.z; the last block
-//           forms beta, tests convergence and sets the loop condition.
+//   matvec: q = Op p and p.q, then alpha = rho / p.q
+//   update: x += alpha p, r -= alpha q, r.z and z.z, then beta, the convergence test
+// An init kernel forms the right-hand side and starts the state; then one persistent
+// kernel, launched cooperatively so that its blocks are co-resident, runs every
+// iteration with grid barriers between the phases (three per iteration), and every block
+// sums the dot products of all blocks in the same fixed order, so that all blocks hold
+// the same scalars and take the same decisions.  Each barrier wait is bounded; a wait
+// that runs out sets a sticky error flag, and every kernel, loop and the host call then
+// stop with an error status.  The phases also exist as single kernels for profiling.
 // The inner kernels are templates on the storage/arithmetic type T: FP64 for the plain
 // path, FP32 for the mixed-precision path (GB300 runs FP32 at 64x its FP64 rate).  Dot
 // products are summed per thread in T and across threads and blocks in FP64.
@@ -18,13 +24,13 @@
 // refinement step runs FCG on S delta = r until ||r|| drops by a fixed factor, then
 // recomputes the true residual r = g - S p with FP64 inner solves.
 // Layout: the vectors of the inner solves are compact, one entry per unknown face (in
-// (a, z, y, x) order) or per fluid cell (in (z, y, x) order), so the streaming kernels
-// are dense, coalesced loops.  Stencil neighbours are found through per-row bitmaps: for
-// every row of nx positions, one 32-bit word per 32 positions and the compact index of
-// that word's first set bit; a neighbour's compact index is base + popcount.  The outer
-// vectors stay dense in cell space (0 on solid cells).
-// All scalars live in the device control block; every loop is a conditional while node
-// of one CUDA graph (or a host loop in debugging mode).  Every loop terminates: each
+// (a, z, y, x) order) or per fluid cell (in (z, y, x) order), so the streaming phases
+// are dense, coalesced loops; stencil neighbours come from per-geometry tables (built
+// from per-row bitmaps: for every row of nx positions, one 32-bit word per 32 positions
+// and the compact index of that word's first set bit, so a rank is base + popcount).  The
+// outer vectors stay dense in cell space (0 on solid cells).
+// All scalars live in the device control block; every outer loop is a conditional while
+// node of one CUDA graph (or a host loop in debugging mode).  Every loop terminates: each
 // condition update either continues below its iteration cap or stops.
 #include <algorithm>
 #include <cmath>
@@ -67,7 +73,7 @@ template <> struct Tab<float> {
 };
 
 __device__ __forceinline__ void note_inner_status(Ctl* ctl, int st) {
-    if (st > ctl->inner_status) ctl->inner_status = st;
+    if (ctl && st > ctl->inner_status) ctl->inner_status = st;
 }
 
 // Finish an inner CG iteration (last block): returns the new loop condition.
@@ -104,14 +110,19 @@ __device__ __forceinline__ unsigned start_inner(Ctl* ctl, CgState* st, double rz
     return 1u;
 }
 
-__device__ __forceinline__ void finish_matvec(Ctl* ctl, CgState* st, double dq, int slot) {
+// alpha = rho / p.q; returns false (breakdown) when p.q is not positive and finite.
+__device__ __forceinline__ bool matvec_alpha(CgState* st, double dq) {
     if (!(dq > 0.0) || isinf(dq)) {
         st->status = ST_BREAKDOWN;
         st->alpha = 0.0;
-        set_cond(ctl, slot, 0u);
-    } else {
-        st->alpha = st->rho / dq;
+        return false;
     }
+    st->alpha = st->rho / dq;
+    return true;
+}
+
+__device__ __forceinline__ void finish_matvec(Ctl* ctl, CgState* st, double dq, int slot) {
+    if (!matvec_alpha(st, dq)) set_cond(ctl, slot, 0u);
 }
 
 // ------------------------------------------------------------------------------------
@@ -302,18 +313,47 @@ __global__ void k_cgA_init(Dev g, Compact C, T* __restrict__ xv, T* __restrict__
         xv[k] = (T)0;
         rv[k] = bt;
     }
-    if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0())
-        set_cond(ctl, slot, start_inner(ctl, st, v[0], v[1]));
+    if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0()) {
+        const unsigned go = start_inner(ctl, st, v[0], v[1]);
+        ctl->bar_count = 0u;  // the loop kernel's grid barrier starts from zero arrivals
+        if (slot >= 0) set_cond(ctl, slot, go);
+    }
 }
+
+// Entries per thread and step of the stencil phases (independent gathers in flight).
+template <typename T> struct MvU { static constexpr int v = 4; };
+template <> struct MvU<double> { static constexpr int v = 2; };
+
+// Per-block copies of the ghost-count tables in shared memory: a lookup is one indexed
+// shared load (no select chain, and nothing for the compiler to keep in registers across
+// the phases of the loop kernel).  w[0] = 0 is the weight of a closed face, w[1 + g] the
+// Jacobi weight 1 / (2d + g), diag[g] = 2d + g.
+template <typename T>
+struct Tabs {
+    T diag[5];
+    T w[6];
+};
+
+template <typename T>
+__device__ __forceinline__ void load_tabs(const Dev& g, Tabs<T>& t) {
+    const int i = threadIdx.x;
+    if (i < 5) {
+        t.diag[i] = Tab<T>::diag(g, i);
+        t.w[i + 1] = Tab<T>::w(g, i);
+    }
+    if (i == 5) t.w[0] = (T)0;
+    __syncthreads();
+}
+
+// The three phases of one inner CG iteration on A', as device functions shared by the
+// single-phase kernels and the persistent loop kernel.  dir and update map entries to
+// threads identically, so a thread only ever touches its own entries between barriers.
 
 // p = M'^-1 r + beta p.
 template <typename T>
-__global__ void k_cgA_dir(Dev g, long long n, const uint8_t* __restrict__ ufl,
-                          const T* __restrict__ rv, T* __restrict__ pv, Ctl* ctl,
-                          const CgState* st) {
-    count_launch(ctl);
+__device__ __forceinline__ void phaseA_dir(const Tabs<T>& t, uint32_t n, const uint8_t* __restrict__ ufl,
+                                           const T* __restrict__ rv, T* __restrict__ pv, T beta) {
     constexpr int kU = StreamU<T>::v;
-    const T beta = (T)(st->first ? 0.0 : st->beta);
     WARP_STREAM_BEGIN_U(n, kU)
         int gh[kU];
         T r[kU], p[kU];
@@ -322,23 +362,17 @@ __global__ void k_cgA_dir(Dev g, long long n, const uint8_t* __restrict__ ufl,
             if (idx[j] < n) { gh[j] = ufl[idx[j]] >> 1; r[j] = rv[idx[j]]; p[j] = pv[idx[j]]; }
 #pragma unroll
         for (int j = 0; j < kU; ++j)
-            if (idx[j] < n) pv[idx[j]] = r[j] * Tab<T>::w(g, gh[j]) + beta * p[j];
+            if (idx[j] < n) pv[idx[j]] = r[j] * t.w[1 + gh[j]] + beta * p[j];
     WARP_STREAM_END
 }
 
-// Entries per thread and step of the stencil kernels (independent gathers in flight).
-template <typename T> struct MvU { static constexpr int v = 4; };
-template <> struct MvU<double> { static constexpr int v = 2; };
-
-// q = A' p and p.q.  The neighbour indices come from the table (coalesced rows); missing
-// neighbours point at the zero entry p[n_u].
+// q = A' p; returns this thread's part of p.q.  The neighbour indices come from the table
+// (coalesced rows); missing neighbours point at the zero entry p[n_u].
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_cgA_matvec(Dev g, Compact C, const T* __restrict__ pv,
-                                                       T* __restrict__ qv, Ctl* ctl, CgState* st,
-                                                       double* partials, int slot) {
-    count_launch(ctl);
+__device__ __forceinline__ T phaseA_matvec(const Tabs<T>& t, const Dev& g, const Compact& C,
+                                           const T* __restrict__ pv, T* __restrict__ qv) {
     T acc = (T)0;
-    const long long n = C.n_u;
+    const uint32_t n = (uint32_t)C.n_u;
     const int ne = 2 * g.d;
     constexpr int U = MvU<T>::v;
     WARP_STREAM_BEGIN_U(n, U)
@@ -350,7 +384,7 @@ __global__ void __launch_bounds__(kBlock) k_cgA_matvec(Dev g, Compact C, const T
             if (idx[j] < n) {
 #pragma unroll
                 for (int e = 0; e < 6; ++e)
-                    nb[j][e] = e < ne ? __ldcs(C.nbA + e * C.ldA + idx[j]) : (uint32_t)n;
+                    nb[j][e] = e < ne ? __ldcs(C.nbA + e * C.ldA + idx[j]) : n;
                 gh[j] = C.ufl[idx[j]] >> 1;
                 pc[j] = pv[idx[j]];
             }
@@ -361,26 +395,21 @@ __global__ void __launch_bounds__(kBlock) k_cgA_matvec(Dev g, Compact C, const T
 #pragma unroll
                 for (int e = 0; e < 6; ++e) sv[e] = pv[nb[j][e]];
                 const T s = ((sv[0] + sv[1]) + (sv[2] + sv[3])) + (sv[4] + sv[5]);
-                const T out = Tab<T>::diag(g, gh[j]) * pc[j] - s;
+                const T out = t.diag[gh[j]] * pc[j] - s;
                 qv[idx[j]] = out;
                 acc += pc[j] * out;
             }
     WARP_STREAM_END
-    double v[1] = {(double)acc};
-    if (reduce_last_block<1>(v, partials, &ctl->ticket) && is_thread0())
-        finish_matvec(ctl, st, v[0], slot);
+    return acc;
 }
 
-// x += alpha p, r -= alpha q; r.z and z.z (z = M'^-1 r).
+// x += alpha p, r -= alpha q; adds this thread's parts of r.z and z.z (z = M'^-1 r).
 template <typename T>
-__global__ void k_cgA_update(Dev g, long long n, const uint8_t* __restrict__ ufl,
-                             T* __restrict__ xv, T* __restrict__ rv, const T* __restrict__ pv,
-                             const T* __restrict__ qv, Ctl* ctl, CgState* st,
-                             double* partials, int slot) {
-    count_launch(ctl);
+__device__ __forceinline__ void phaseA_update(const Tabs<T>& t, uint32_t n, const uint8_t* __restrict__ ufl,
+                                              T* __restrict__ xv, T* __restrict__ rv,
+                                              const T* __restrict__ pv, const T* __restrict__ qv,
+                                              T alpha, T& a0, T& a1) {
     constexpr int kU = StreamU<T>::v;
-    const T alpha = (T)st->alpha;
-    T a0 = (T)0, a1 = (T)0;
     WARP_STREAM_BEGIN_U(n, kU)
         int gh[kU];
         T xx[kU], p[kU], r[kU], q[kU];
@@ -399,11 +428,46 @@ __global__ void k_cgA_update(Dev g, long long n, const uint8_t* __restrict__ ufl
                 xv[idx[j]] = xx[j] + alpha * p[j];
                 const T rn = r[j] - alpha * q[j];
                 rv[idx[j]] = rn;
-                const T zz = rn * Tab<T>::w(g, gh[j]);
+                const T zz = rn * t.w[1 + gh[j]];
                 a0 += rn * zz;
                 a1 += zz * zz;
             }
     WARP_STREAM_END
+}
+
+// Single-phase kernels (one launch per phase; the profiling hook times them one by one).
+template <typename T>
+__global__ void k_cgA_dir(Dev g, long long n, const uint8_t* __restrict__ ufl,
+                          const T* __restrict__ rv, T* __restrict__ pv, Ctl* ctl,
+                          const CgState* st) {
+    count_launch(ctl);
+    __shared__ Tabs<T> t;
+    load_tabs<T>(g, t);
+    phaseA_dir<T>(t, (uint32_t)n, ufl, rv, pv, (T)(st->first ? 0.0 : st->beta));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cgA_matvec(Dev g, Compact C, const T* __restrict__ pv,
+                                                       T* __restrict__ qv, Ctl* ctl, CgState* st,
+                                                       double* partials, int slot) {
+    count_launch(ctl);
+    __shared__ Tabs<T> t;
+    load_tabs<T>(g, t);
+    double v[1] = {(double)phaseA_matvec<T>(t, g, C, pv, qv)};
+    if (reduce_last_block<1>(v, partials, &ctl->ticket) && is_thread0())
+        finish_matvec(ctl, st, v[0], slot);
+}
+
+template <typename T>
+__global__ void k_cgA_update(Dev g, long long n, const uint8_t* __restrict__ ufl,
+                             T* __restrict__ xv, T* __restrict__ rv, const T* __restrict__ pv,
+                             const T* __restrict__ qv, Ctl* ctl, CgState* st,
+                             double* partials, int slot) {
+    count_launch(ctl);
+    __shared__ Tabs<T> t;
+    load_tabs<T>(g, t);
+    T a0 = (T)0, a1 = (T)0;
+    phaseA_update<T>(t, (uint32_t)n, ufl, xv, rv, pv, qv, (T)st->alpha, a0, a1);
     double v[2] = {(double)a0, (double)a1};
     if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0())
         set_cond(ctl, slot, finish_inner(ctl, st, v[0], v[1]));
@@ -422,7 +486,7 @@ __global__ void k_cgS_init(Dev g, Compact C, const T* __restrict__ invd, const i
                            const CgState* outer, double* partials, int slot) {
     count_launch(ctl);
     if (outer->skip_next) {
-        if (blockIdx.x == 0 && is_thread0()) set_cond(ctl, slot, 0u);
+        if (blockIdx.x == 0 && is_thread0() && slot >= 0) set_cond(ctl, slot, 0u);
         return;
     }
     double v[2] = {0.0, 0.0};
@@ -437,16 +501,17 @@ __global__ void k_cgS_init(Dev g, Compact C, const T* __restrict__ invd, const i
         xv[m] = (T)0;
         rv[m] = bt;
     }
-    if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0())
-        set_cond(ctl, slot, start_inner(ctl, st, v[0], v[1]));
+    if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0()) {
+        const unsigned go = start_inner(ctl, st, v[0], v[1]);
+        ctl->bar_count = 0u;  // the loop kernel's grid barrier starts from zero arrivals
+        if (slot >= 0) set_cond(ctl, slot, go);
+    }
 }
 
 template <typename T>
-__global__ void k_cgS_dir(Dev g, long long n, const T* __restrict__ invd, const T* __restrict__ rv,
-                          T* __restrict__ pv, Ctl* ctl, const CgState* st) {
-    count_launch(ctl);
+__device__ __forceinline__ void phaseS_dir(uint32_t n, const T* __restrict__ invd,
+                                           const T* __restrict__ rv, T* __restrict__ pv, T beta) {
     constexpr int kU = StreamU<T>::v;
-    const T beta = (T)(st->first ? 0.0 : st->beta);
     WARP_STREAM_BEGIN_U(n, kU)
         T r[kU], w[kU], p[kU];
 #pragma unroll
@@ -458,23 +523,16 @@ __global__ void k_cgS_dir(Dev g, long long n, const T* __restrict__ invd, const 
     WARP_STREAM_END
 }
 
-// Weight 1 / (2d + g) of an open face from its 3-bit code (0: closed face, weight 0).
+// q = S-hat p; returns this thread's part of p.q.  FP64 (bound by the FP64 pipe) forms
+// diag(S-hat) p_c minus the weighted neighbour sum; FP32 sums the weighted differences
+// (p_c - p_nb), which vanish exactly on constants.  Closed faces point at the zero entry
+// p[n_p] with weight 0.
 template <typename T>
-__device__ __forceinline__ T face_weight(const Dev& g, uint32_t code) {
-    return code == 0u ? (T)0 : Tab<T>::w(g, (int)code - 1);
-}
-
-// q = S-hat p and p.q.  FP64 (bound by the FP64 pipe) forms diag(S-hat) p_c minus the
-// weighted neighbour sum; FP32 sums the weighted differences (p_c - p_nb), which vanish
-// exactly on constants.  Closed faces point at the zero entry p[n_p] with weight 0.
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_cgS_matvec(Dev g, Compact C, const T* __restrict__ dS,
-                                                       const T* __restrict__ pv, T* __restrict__ qv,
-                                                       Ctl* ctl, CgState* st, double* partials,
-                                                       int slot) {
-    count_launch(ctl);
+__device__ __forceinline__ T phaseS_matvec(const Tabs<T>& t, const Dev& g, const Compact& C,
+                                           const T* __restrict__ dS, const T* __restrict__ pv,
+                                           T* __restrict__ qv) {
     T acc = (T)0;
-    const long long n = C.n_p;
+    const uint32_t n = (uint32_t)C.n_p;
     const int ne = 2 * g.d;
     constexpr int U = MvU<T>::v;
     WARP_STREAM_BEGIN_U(n, U)
@@ -485,7 +543,7 @@ __global__ void __launch_bounds__(kBlock) k_cgS_matvec(Dev g, Compact C, const T
             if (idx[j] < n) {
 #pragma unroll
                 for (int e = 0; e < 6; ++e)
-                    nb[j][e] = e < ne ? __ldcs(C.nbS + e * C.ldS + idx[j]) : (uint32_t)n;
+                    nb[j][e] = e < ne ? __ldcs(C.nbS + e * C.ldS + idx[j]) : n;
                 code[j] = __ldcs(C.codeS + idx[j]);
                 pc[j] = pv[idx[j]];
                 if constexpr (sizeof(T) == 8) dg[j] = dS[idx[j]];
@@ -498,34 +556,28 @@ __global__ void __launch_bounds__(kBlock) k_cgS_matvec(Dev g, Compact C, const T
                 for (int e = 0; e < 6; ++e) sv[e] = pv[nb[j][e]];
                 T out;
                 if constexpr (sizeof(T) == 8) {
-                    T s = face_weight<T>(g, code[j] & 7u) * sv[0];
+                    T s = t.w[code[j] & 7u] * sv[0];
 #pragma unroll
-                    for (int e = 1; e < 6; ++e) s += face_weight<T>(g, (code[j] >> (3 * e)) & 7u) * sv[e];
+                    for (int e = 1; e < 6; ++e) s += t.w[(code[j] >> (3 * e)) & 7u] * sv[e];
                     out = dg[j] * pc[j] - s;
                 } else {
                     out = (T)0;
 #pragma unroll
                     for (int e = 0; e < 6; ++e)
-                        out += face_weight<T>(g, (code[j] >> (3 * e)) & 7u) * (pc[j] - sv[e]);
+                        out += t.w[(code[j] >> (3 * e)) & 7u] * (pc[j] - sv[e]);
                 }
                 qv[idx[j]] = out;
                 acc += pc[j] * out;
             }
     WARP_STREAM_END
-    double v[1] = {(double)acc};
-    if (reduce_last_block<1>(v, partials, &ctl->ticket) && is_thread0())
-        finish_matvec(ctl, st, v[0], slot);
+    return acc;
 }
 
 template <typename T>
-__global__ void k_cgS_update(Dev g, long long n, const T* __restrict__ invd, T* __restrict__ xv,
-                             T* __restrict__ rv, const T* __restrict__ pv,
-                             const T* __restrict__ qv, Ctl* ctl, CgState* st,
-                             double* partials, int slot) {
-    count_launch(ctl);
+__device__ __forceinline__ void phaseS_update(uint32_t n, const T* __restrict__ invd, T* __restrict__ xv,
+                                              T* __restrict__ rv, const T* __restrict__ pv,
+                                              const T* __restrict__ qv, T alpha, T& a0, T& a1) {
     constexpr int kU = StreamU<T>::v;
-    const T alpha = (T)st->alpha;
-    T a0 = (T)0, a1 = (T)0;
     WARP_STREAM_BEGIN_U(n, kU)
         T xx[kU], p[kU], r[kU], q[kU], w[kU];
 #pragma unroll
@@ -548,9 +600,199 @@ __global__ void k_cgS_update(Dev g, long long n, const T* __restrict__ invd, T* 
                 a1 += zz * zz;
             }
     WARP_STREAM_END
+}
+
+template <typename T>
+__global__ void k_cgS_dir(Dev g, long long n, const T* __restrict__ invd, const T* __restrict__ rv,
+                          T* __restrict__ pv, Ctl* ctl, const CgState* st) {
+    count_launch(ctl);
+    phaseS_dir<T>((uint32_t)n, invd, rv, pv, (T)(st->first ? 0.0 : st->beta));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cgS_matvec(Dev g, Compact C, const T* __restrict__ dS,
+                                                       const T* __restrict__ pv, T* __restrict__ qv,
+                                                       Ctl* ctl, CgState* st, double* partials,
+                                                       int slot) {
+    count_launch(ctl);
+    __shared__ Tabs<T> t;
+    load_tabs<T>(g, t);
+    double v[1] = {(double)phaseS_matvec<T>(t, g, C, dS, pv, qv)};
+    if (reduce_last_block<1>(v, partials, &ctl->ticket) && is_thread0())
+        finish_matvec(ctl, st, v[0], slot);
+}
+
+template <typename T>
+__global__ void k_cgS_update(Dev g, long long n, const T* __restrict__ invd, T* __restrict__ xv,
+                             T* __restrict__ rv, const T* __restrict__ pv,
+                             const T* __restrict__ qv, Ctl* ctl, CgState* st,
+                             double* partials, int slot) {
+    count_launch(ctl);
+    T a0 = (T)0, a1 = (T)0;
+    phaseS_update<T>((uint32_t)n, invd, xv, rv, pv, qv, (T)st->alpha, a0, a1);
     double v[2] = {(double)a0, (double)a1};
     if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0())
         set_cond(ctl, slot, finish_inner(ctl, st, v[0], v[1]));
+}
+
+// ------------------------------------------------------------------------------------
+// persistent inner CG: one cooperative launch runs every iteration of an inner solve
+// ------------------------------------------------------------------------------------
+// The grid stays resident (one wave: the grid never exceeds the kernel's resident
+// blocks), the phases are separated by grid barriers, and the dot products are summed
+// by every block in the same fixed order, so all blocks hold bitwise-equal Krylov scalars
+// and take the same decisions without writing them back between phases.  Three barriers
+// per iteration replace three kernel launches and a conditional graph node.
+
+// Block sum of K doubles, result in every thread (one warp adds through shared memory).
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K]) {
+    __shared__ double sm[K][kBlock];
+    __shared__ double out[K];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nthr = blockDim.x;
+#pragma unroll
+    for (int k = 0; k < K; ++k) sm[k][tid] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double x = 0.0;
+            for (int j = lane; j < nthr; j += 32) x += sm[k][j];
+            x = warp_sum(x);
+            if (lane == 0) out[k] = x;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = out[k];
+    __syncthreads();
+}
+
+// Grid sum of K doubles, identical in every block: block sums go to part[block][K], all
+// blocks meet at a barrier, then each block adds the gridDim.x partials in a fixed order.
+// Returns false when the barrier failed.
+template <int K>
+__device__ __forceinline__ bool grid_sum(double (&v)[K], double* part, Ctl* ctl, unsigned& target) {
+    block_sum<K>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) part[(size_t)blockIdx.x * K + k] = v[k];
+    }
+    if (!grid_barrier(ctl, target)) return false;
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] += __ldcg(&part[(size_t)i * K + k]);
+    }
+    block_sum<K>(acc);
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = acc[k];
+    return true;
+}
+
+// Hides a value from the optimiser for one loop iteration, so that addresses derived
+// from it are recomputed in each phase instead of being kept in registers across all
+// phases of the loop kernel (which would cut its occupancy to two blocks per SM).
+template <class P>
+__device__ __forceinline__ P* opaque(P* p) {
+    asm volatile("" : "+l"(p));
+    return p;
+}
+__device__ __forceinline__ uint32_t opaque_u32(uint32_t v) {
+    asm volatile("" : "+r"(v));
+    return v;
+}
+
+// The loop of an inner solve after its init kernel: `st` holds the started state (status
+// NOTCONV when iterations are due).  `gate` (may be null) skips the whole solve when set.
+// Ends with st written back by block 0 and ctl->inner_status updated as the single-phase
+// kernels do; a failed barrier leaves status ST_BARRIER.
+template <typename T, bool kS>
+__device__ __forceinline__ void cg_loop(const Dev& g, const Compact& C, const T* __restrict__ aux,
+                                        const T* __restrict__ dS, T* __restrict__ xv, T* __restrict__ rv, T* __restrict__ pv,
+                                        T* __restrict__ qv, Ctl* ctl, CgState* st, double* partials,
+                                        const int* gate) {
+    __shared__ CgState s;
+    __shared__ unsigned s_cont;
+    __shared__ Tabs<T> t;
+    if (gate && *gate) return;
+    load_tabs<T>(g, t);
+    if (threadIdx.x == 0) s = *st;
+    __syncthreads();
+    if (s.status != ST_NOTCONV || ld_acquire_u32(&ctl->bar_err) != 0u) return;
+    const uint32_t n = (uint32_t)(kS ? C.n_p : C.n_u);
+    double* P1 = partials;               // [grid] p.q
+    double* P2 = partials + kMaxBlocks;  // [grid][2] r.z, z.z
+    unsigned target = 0;
+    bool ok = true;
+    for (;;) {
+        const T beta = (T)(s.first ? 0.0 : s.beta);
+        if constexpr (kS) phaseS_dir<T>(opaque_u32(n), opaque(aux), opaque(rv), opaque(pv), beta);
+        else phaseA_dir<T>(t, opaque_u32(n), opaque(C.ufl), opaque(rv), opaque(pv), beta);
+        if (!(ok = grid_barrier(ctl, target))) break;
+        double v1[1];
+        {
+            Compact Cl = C;
+            Cl.nbA = opaque(C.nbA);
+            Cl.nbS = opaque(C.nbS);
+            Cl.codeS = opaque(C.codeS);
+            Cl.ufl = opaque(C.ufl);
+            if constexpr (kS) v1[0] = (double)phaseS_matvec<T>(t, g, Cl, opaque(dS), opaque(pv), opaque(qv));
+            else v1[0] = (double)phaseA_matvec<T>(t, g, Cl, opaque(pv), opaque(qv));
+        }
+        if (!(ok = grid_sum<1>(v1, P1, ctl, target))) break;
+        if (threadIdx.x == 0) {
+            s_cont = matvec_alpha(&s, v1[0]) ? 1u : 0u;
+            if (!s_cont) finish_inner(nullptr, &s, 0.0, 0.0);  // counts the iteration
+        }
+        __syncthreads();
+        if (!s_cont) break;
+        T a0 = (T)0, a1 = (T)0;
+        if constexpr (kS)
+            phaseS_update<T>(opaque_u32(n), opaque(aux), opaque(xv), opaque(rv), opaque(pv),
+                             opaque(qv), (T)s.alpha, a0, a1);
+        else
+            phaseA_update<T>(t, opaque_u32(n), opaque(C.ufl), opaque(xv), opaque(rv), opaque(pv),
+                             opaque(qv), (T)s.alpha, a0, a1);
+        double v2[2] = {(double)a0, (double)a1};
+        if (!(ok = grid_sum<2>(v2, P2, ctl, target))) break;
+        if (threadIdx.x == 0) s_cont = finish_inner(nullptr, &s, v2[0], v2[1]);
+        __syncthreads();
+        if (!s_cont) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (!ok) s.status = ST_BARRIER;
+        *st = s;
+        note_inner_status(ctl, s.status);
+    }
+}
+
+// Minimum resident blocks per SM asked of the loop kernels: 3 for FP64 (pipe-bound, the
+// phases fit in 85 registers), 2 for FP32 (a lower bound spills the stencil's gathers).
+template <typename T> struct LoopMinBlocks { static constexpr int v = 2; };
+template <> struct LoopMinBlocks<double> { static constexpr int v = 3; };
+
+// aux: unused for A; invd (Jacobi weights of S-hat) for S.  dS: diagonal of S-hat (read by
+// the FP64 S matvec).
+template <typename T>
+__global__ void __launch_bounds__(kBlock, LoopMinBlocks<T>::v) k_cgA_loop(Dev g, Compact C, T* __restrict__ xv,
+                                                     T* __restrict__ rv, T* __restrict__ pv,
+                                                     T* __restrict__ qv, Ctl* ctl, CgState* st,
+                                                     double* partials) {
+    count_launch(ctl);
+    cg_loop<T, false>(g, C, nullptr, nullptr, xv, rv, pv, qv, ctl, st, partials, nullptr);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock, LoopMinBlocks<T>::v) k_cgS_loop(Dev g, Compact C, const T* __restrict__ invd,
+                                                     const T* __restrict__ dS, T* __restrict__ xv,
+                                                     T* __restrict__ rv, T* __restrict__ pv,
+                                                     T* __restrict__ qv, Ctl* ctl, CgState* st,
+                                                     double* partials, const int* gate) {
+    count_launch(ctl);
+    cg_loop<T, true>(g, C, invd, dS, xv, rv, pv, qv, ctl, st, partials, gate);
 }
 
 // ------------------------------------------------------------------------------------
@@ -748,7 +990,10 @@ __global__ void k_outer_update(Dev g, double* __restrict__ pv, double* __restric
         const double rel = sqrt(v[0] / o->rr0);
         o->rel = rel;
         unsigned cont = 1u;
-        if (ctl->stop_norm == 0 && rel < o->tol) {
+        if (ctl->bar_err) {
+            o->status = ST_BARRIER;  // an inner solve failed: stop
+            cont = 0u;
+        } else if (ctl->stop_norm == 0 && rel < o->tol) {
             o->status = ST_OK;
             o->relz = nan("");
             cont = 0u;
@@ -926,7 +1171,7 @@ __global__ void k_fcg_update(Dev g, double* __restrict__ pv, double* __restrict_
         const double f2 = m.factor * m.factor;
         const int done = (v[0] <= f2 * m.rr_step0) || (v[0] < o->tol * o->tol * o->rr0) ||
                          (m.step_iter >= m.step_max) || (o->iter >= o->max_iter) ||
-                         !(v[0] == v[0]);
+                         !(v[0] == v[0]) || ctl->bar_err;
         if (done) {
             o->skip_next = 1;
             set_cond(ctl, slot, 0u);
@@ -977,7 +1222,10 @@ __global__ void k_true_res(Dev g, Compact C, const uint8_t* __restrict__ mask,
         o->rel = rel;
         m.refine += 1;
         unsigned cont = 1u;
-        if (rel < o->tol) {
+        if (ctl->bar_err) {
+            o->status = ST_BARRIER;
+            cont = 0u;
+        } else if (rel < o->tol) {
             o->status = ST_OK;
             cont = 0u;
         } else if (!(rel == rel)) {
@@ -1095,16 +1343,10 @@ static void record_A_solve(Handle& H, Recorder& R, InnerA<T> v, CgState* st, int
     const Compact C = compact_of(H);
     const long long nu = H.n_u;
     R.launch("cgA_init", k_cgA_init<T>, sgrid(H, nu, k_cgA_init<T>), sblock(), H.g, C, v.x, v.r, P, cp, cf,
-             bvec, H.dctl, st, H.partials, s);
-    R.loop(s, [&H, C, v, st, s, nu](Recorder& B) {
-        B.launch("cgA_dir", k_cgA_dir<T>, sgrid(H, nu, k_cgA_dir<T>), sblock(), H.g, nu, (const uint8_t*)H.ufl,
-                 (const T*)v.r, v.p, H.dctl, (const CgState*)st);
-        B.launch("cgA_matvec", k_cgA_matvec<T>, sgrid(H, nu, k_cgA_matvec<T>), sblock(), H.g, C, (const T*)v.p, v.q,
-                 H.dctl, st, H.partials, s);
-        B.launch("cgA_update", k_cgA_update<T>, sgrid(H, nu, k_cgA_update<T>), sblock(), H.g, nu,
-                 (const uint8_t*)H.ufl, v.x, v.r, (const T*)v.p, (const T*)v.q, H.dctl, st,
-                 H.partials, s);
-    });
+             bvec, H.dctl, st, H.partials, -1);
+    (void)s;
+    R.launch_coop("cgA_loop", k_cgA_loop<T>, sgrid(H, nu, k_cgA_loop<T>), sblock(), H.g, C, v.x,
+                  v.r, v.p, v.q, H.dctl, st, H.partials);
 }
 
 template <typename T>
@@ -1131,15 +1373,11 @@ static void record_S_solve(Handle& H, Recorder& R, InnerS<T> v, CgState* st, int
     record_comp_means<double>(H, R, H.orr, 1);
     R.launch("cgS_init", k_cgS_init<T>, sgrid(H, np, k_cgS_init<T>), sblock(), H.g, C, v.invd,
              (const int*)H.cmpc, (const double*)H.cmean, H.orr, v.x, v.r, H.dctl, st,
-             (const CgState*)&H.dctl->out, H.partials, s);
-    R.loop(s, [&H, C, v, st, s, np](Recorder& B) {
-        B.launch("cgS_dir", k_cgS_dir<T>, sgrid(H, np, k_cgS_dir<T>), sblock(), H.g, np, v.invd, (const T*)v.r,
-                 v.p, H.dctl, (const CgState*)st);
-        B.launch("cgS_matvec", k_cgS_matvec<T>, sgrid(H, np, k_cgS_matvec<T>), sblock(), H.g, C,
-                 v.diag, (const T*)v.p, v.q, H.dctl, st, H.partials, s);
-        B.launch("cgS_update", k_cgS_update<T>, sgrid(H, np, k_cgS_update<T>), sblock(), H.g, np, v.invd, v.x, v.r,
-                 (const T*)v.p, (const T*)v.q, H.dctl, st, H.partials, s);
-    });
+             (const CgState*)&H.dctl->out, H.partials, -1);
+    (void)s;
+    R.launch_coop("cgS_loop", k_cgS_loop<T>, sgrid(H, np, k_cgS_loop<T>), sblock(), H.g, C,
+                  v.invd, v.diag, v.x, v.r, v.p, v.q, H.dctl, st, H.partials,
+                  (const int*)&H.dctl->out.skip_next);
     record_comp_means<T>(H, R, (const T*)v.x, 0);
 }
 
@@ -1263,17 +1501,77 @@ void record_solve_A(Handle& H, Recorder& R, const double* b, double* x) {
 // kernels read and write the solver's own buffers; the solo CG state absorbs the
 // scalars).  which: 0-5 FP64 A dir/matvec/update and S dir/matvec/update; 6-11 the same
 // in FP32 (the mixed-precision buffers must exist).
+// Deterministic right-hand side for timing the SIMPLE loop: hashed values in [-0.5, 0.5).
+__global__ void k_fill_pattern(double* __restrict__ v, long long n) {
+    STREAM_LOOP(i, n) v[i] = (double)(((uint32_t)i * 2654435761u) >> 12) / 1048576.0 - 0.5;
+}
+
+// One cooperative launch of a persistent inner-CG kernel running exactly
+// SCHUR_TIMED_LOOP_ITERS iterations (tolerance 0) from a fixed right-hand side: the A loop
+// from b = f, the SIMPLE loop from a hashed cell vector.  Only the loop launch is timed.
+template <typename T>
+static cudaError_t time_loop_t(Handle& H, bool simple, InnerA<T> a, InnerS<T> sv, float* ms) {
+    Ctl* ctl = H.dctl;
+    CgState* st = &ctl->solo;
+    const Compact C = compact_of(H);
+    H.hctl->solo.tol = 0.0;
+    H.hctl->solo.max_iter = SCHUR_TIMED_LOOP_ITERS;
+    H.hctl->solo.skip_next = 0;
+    cudaError_t e = cudaMemcpyAsync(&ctl->solo, &H.hctl->solo, sizeof(CgState),
+                                    cudaMemcpyHostToDevice, H.stream);
+    if (e != cudaSuccess) return e;
+    const dim3 b = sblock();
+    if (!simple) {
+        k_cgA_init<T><<<sgrid(H, H.n_u, k_cgA_init<T>), b, 0, H.stream>>>(
+            H.g, C, a.x, a.r, nullptr, 0.0, 1.0, nullptr, ctl, st, H.partials, -1);
+    } else {
+        k_fill_pattern<<<sgrid(H, H.g.ncell, k_fill_pattern), b, 0, H.stream>>>(H.orr, H.g.ncell);
+        k_cgS_init<T><<<sgrid(H, H.n_p, k_cgS_init<T>), b, 0, H.stream>>>(
+            H.g, C, sv.invd, H.cmpc, H.cmean, H.orr, sv.x, sv.r, ctl, st, st, H.partials, -1);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(H.ev0, H.stream)) != cudaSuccess) return e;
+    if (!simple) {
+        void* args[] = {(void*)&H.g, (void*)&C, (void*)&a.x, (void*)&a.r, (void*)&a.p, (void*)&a.q,
+                        (void*)&ctl, (void*)&st, (void*)&H.partials};
+        e = cudaLaunchCooperativeKernel((const void*)k_cgA_loop<T>, sgrid(H, H.n_u, k_cgA_loop<T>), b,
+                                        args, 0, H.stream);
+    } else {
+        const int* gate = nullptr;
+        void* args[] = {(void*)&H.g, (void*)&C, (void*)&sv.invd, (void*)&sv.diag, (void*)&sv.x,
+                        (void*)&sv.r, (void*)&sv.p, (void*)&sv.q, (void*)&ctl, (void*)&st,
+                        (void*)&H.partials, (void*)&gate};
+        e = cudaLaunchCooperativeKernel((const void*)k_cgS_loop<T>, sgrid(H, H.n_p, k_cgS_loop<T>), b,
+                                        args, 0, H.stream);
+    }
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(H.ev1, H.stream)) != cudaSuccess) return e;
+    if ((e = cudaEventSynchronize(H.ev1)) != cudaSuccess) return e;
+    return cudaEventElapsedTime(ms, H.ev0, H.ev1);
+}
+
+static cudaError_t time_loop(Handle& H, int which, float* ms) {
+    switch (which) {
+        case 12: return time_loop_t<double>(H, false, innerA64(H), innerS64(H), ms);
+        case 13: return time_loop_t<double>(H, true, innerA64(H), innerS64(H), ms);
+        case 14: return time_loop_t<float>(H, false, innerA32(H), innerS32(H), ms);
+        case 15: return time_loop_t<float>(H, true, innerA32(H), innerS32(H), ms);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t time_kernel(Handle& H, int which, int slot, float* ms) {
     if (!H.ev0) {
         cudaError_t e = cudaEventCreate(&H.ev0);
         if (e == cudaSuccess) e = cudaEventCreate(&H.ev1);
         if (e != cudaSuccess) return e;
     }
-    if (which >= 6 && !H.axf) return cudaErrorInvalidValue;
+    if (((which >= 6 && which < 12) || which >= 14) && !H.axf) return cudaErrorInvalidValue;
     Ctl* ctl = H.dctl;
     CgState* st = &ctl->solo;
     const long long nu = H.n_u, np = H.n_p;
     const Compact C = compact_of(H);
+    if (which >= 12) return time_loop(H, which, ms);
     cudaError_t e = cudaEventRecord(H.ev0, H.stream);
     if (e != cudaSuccess) return e;
     const dim3 b = sblock();

@@ -134,7 +134,9 @@ extern "C" int schur_batch_run(schur_batch_t b, schur_stats* solve_stats,
         if (k_out)
             for (int a = 0; a < 3; ++a) k_out[3 * i + a] = H.hctl->perm[a];
         const int s1 = H.hctl->out.status, s2 = H.hctl->rec.status;
-        if (s1 == ST_BREAKDOWN || s2 == ST_BREAKDOWN) worst = SCHUR_EBREAKDOWN;
+        if (H.hctl->bar_err) worst = SCHUR_ECUDA;
+        else if (worst == SCHUR_ECUDA) continue;
+        else if (s1 == ST_BREAKDOWN || s2 == ST_BREAKDOWN) worst = SCHUR_EBREAKDOWN;
         else if ((s1 != ST_OK || s2 != ST_OK) && worst == SCHUR_OK) worst = SCHUR_ENOTCONV;
     }
     if (worst != SCHUR_OK) schur_set_error_internal(worst, "a batch member did not converge");
