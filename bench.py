@@ -592,13 +592,19 @@ def batch_pattern(binding, torch, masks, stream):
     opts = dict(precond=binding.UZAWA, precision=binding.MIXED, tol=1e-8)
     geoms = [binding.Geometry(torch.from_numpy(m).cuda()) for m in masks]
     best, tune_ms = binding.Batch.autotune(geoms[:8], **opts)
-    b = binding.Batch(geoms, blocks_per_sm=best, **opts)
+    for g in geoms[8:]:
+        g.set_launch(*best)
+    b = binding.Batch(geoms, blocks_per_sm=0, **opts)
     b.run()                                             # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ss, rs, ks = b.run()
     t_batch = time.perf_counter() - t0
     b.close()
+    for g in geoms:
+        g.set_launch(8, 1, 1)                           # single-solve shape
+        g.solve(**opts)                                 # warm-up (graph recording)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     for g in geoms:
         g.solve(**opts)
@@ -614,7 +620,8 @@ def batch_pattern(binding, torch, masks, stream):
         g.close()
     return {"n_geometries": len(masks), "edges": sorted({m.shape[0] for m in masks}),
             "cells_total": int(sum(cells)), "precond": "uzawa", "precision": "mixed",
-            "autotuned_blocks_per_sm": best, "batch_s": t_batch,
+            "autotuned_shape": {"blocks_per_sm": best[0], "entries_per_thread": best[1],
+                                "persistent_inner": best[2]}, "batch_s": t_batch,
             "batch_solves_per_s": len(masks) / t_batch,
             "sequential_mixed_solves_per_s": len(masks) / t_seq,
             "sequential_fp64_solves_per_s_first8": 1.0 / t_seq64,

@@ -195,6 +195,18 @@ int schur_solve_A(schur_geom_t g, const double* b, double* x, double tol, int ma
 #define SCHUR_TIMED_LOOP_ITERS 20
 int schur_time_kernel(schur_geom_t g, int kernel, float* ms);
 
+/* Launch shape of a geometry's kernels: grids are capped at blocks_per_sm (1..32) x SMs
+ * (and at the kernel's resident blocks) and give every thread at least
+ * entries_per_thread (1..4096) entries; persistent_inner = 1 runs every inner solve as one
+ * cooperative loop kernel, 0 as one graph node per CG phase inside a conditional while
+ * node.  Default (8, 1, 1): one wave over the whole GPU, the fastest single solve.
+ * Results depend on the shape only through the order of the floating-point reductions;
+ * equal shapes give bitwise-equal results.  Drops the recorded graphs (they are rebuilt
+ * on the next call).  Errors: SCHUR_EINVAL (range), SCHUR_ESTATE (an asynchronous solve
+ * is in flight). */
+int schur_set_launch(schur_geom_t g, int blocks_per_sm, int entries_per_thread,
+                     int persistent_inner);
+
 /* Allocation-free Darcy permeability of a caller-owned velocity field (no counterpart in
  * the paper: an entry point for callers that may not allocate device memory, e.g. code
  * running inside a memory pool it does not own or inside an already-captured graph).
@@ -215,17 +227,22 @@ int schur_permeability_noalloc(const double* u, const uint8_t* flags, int ndim,
 /* ---- batched execution -------------------------------------------------------------
  * The solve + recovery of n geometries recorded as n parallel branches of ONE CUDA graph
  * (one cudaGraphLaunch runs all of them; the GPU overlaps the branches).  The handles
- * must stay alive and are used on `stream`; blocks_per_sm (1..32) sets the grid of
- * every kernel to blocks_per_sm x SMs.  schur_batch_run launches the graph, waits, and
- * fills n solve / recovery stats and 3n permeabilities (each output may be NULL); it
- * returns the worst status.  schur_batch_autotune times the batch for blocks_per_sm in
- * {2, 4, 8, 16} and leaves the geometries on the fastest. */
+ * must stay alive and are used on `stream`.  blocks_per_sm in 1..32 gives every geometry
+ * the launch shape (blocks_per_sm, 16 entries per thread, persistent inner loops) (see
+ * schur_set_launch): small geometries then take a few SMs and the branches overlap;
+ * blocks_per_sm = 0 keeps each geometry's current shape.  schur_batch_run launches the
+ * graph, waits, and fills n solve / recovery stats and 3n permeabilities (each output may
+ * be NULL); it returns the worst status.  schur_batch_autotune times the batch for a few
+ * launch shapes (per-phase graph nodes and persistent loops, several grid sizes), leaves
+ * the geometries on the fastest and writes it to best_shape = {blocks_per_sm,
+ * entries_per_thread, persistent_inner}; create the batch with blocks_per_sm = 0 to run
+ * it. */
 int schur_batch_create(schur_geom_t* geoms, int n, const schur_opts* opts, int blocks_per_sm,
                        void* stream, schur_batch_t* out);
 int schur_batch_run(schur_batch_t b, schur_stats* solve_stats, schur_stats* recover_stats,
                     double* k_out);
 int schur_batch_autotune(schur_geom_t* geoms, int n, const schur_opts* opts, void* stream,
-                         int* best_blocks_per_sm, double* best_ms);
+                         int best_shape[3], double* best_ms);
 void schur_batch_destroy(schur_batch_t b);
 
 /* ---- serving --------------------------------------------------------------------------
@@ -233,7 +250,9 @@ void schur_batch_destroy(schur_batch_t b);
  * (host mask copied; unit force along `axis`); schur_server_progress admits queued jobs in
  * arrival order while their estimated device footprint (schur_footprint_bytes) fits the
  * budget and fewer than max_active run, launches each on its own stream (geometry +
- * asynchronous solve + recovery), and collects finished ones without blocking;
+ * asynchronous solve + recovery, launch shape (8, 1, 0) of schur_set_launch: per-phase
+ * graph nodes, so that the jobs in flight interleave), and collects finished ones without
+ * blocking;
  * schur_server_take returns finished results.  Times are seconds since creation. */
 typedef struct {
     int64_t id;

@@ -33,6 +33,7 @@ EXPORTED = [
     "schur_batch_destroy", "schur_footprint_bytes", "schur_server_create",
     "schur_server_submit", "schur_server_progress", "schur_server_take", "schur_server_info",
     "schur_server_destroy",
+    "schur_set_launch",
 ]
 KERNELS = {"cgA_dir": 0, "cgA_matvec": 1, "cgA_update": 2, "cgS_dir": 3, "cgS_matvec": 4,
            "cgS_update": 5, "cgA_dir_f32": 6, "cgA_matvec_f32": 7, "cgA_update_f32": 8,
@@ -109,6 +110,7 @@ def load(build_if_missing: bool = True):
         "schur_apply_simple": (C.c_int, [vp, vp, vp]),
         "schur_solve_A": (C.c_int, [vp, vp, vp, C.c_double, C.c_int, C.POINTER(C.c_int)]),
         "schur_time_kernel": (C.c_int, [vp, C.c_int, C.POINTER(C.c_float)]),
+        "schur_set_launch": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
         "schur_permeability_noalloc": (C.c_int, [vp, vp, C.c_int, i64p, C.c_int64, vp, vp]),
         "schur_solve_async": (C.c_int, [vp, C.POINTER(Opts)]),
         "schur_query": (C.c_int, [vp, C.POINTER(C.c_int)]),
@@ -118,7 +120,7 @@ def load(build_if_missing: bool = True):
         "schur_batch_run": (C.c_int, [vp, C.POINTER(Stats), C.POINTER(Stats),
                                       C.POINTER(C.c_double)]),
         "schur_batch_autotune": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(Opts), vp,
-                                           C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+                                           C.POINTER(C.c_int * 3), C.POINTER(C.c_double)]),
         "schur_batch_destroy": (None, [vp]),
         "schur_footprint_bytes": (C.c_int64, [C.c_int, i64p, C.c_int]),
         "schur_server_create": (C.c_int, [C.POINTER(Opts), C.c_int64, C.c_int, C.POINTER(vp)]),
@@ -302,6 +304,10 @@ class Geometry:
         _check(load().schur_solve_A(self._h, _ptr(b), _ptr(x), tol, max_iter, C.byref(it)))
         return it.value
 
+    def set_launch(self, blocks_per_sm=8, entries_per_thread=1, persistent=1):
+        """Launch shape of this geometry's kernels (see schur_set_launch)."""
+        _check(load().schur_set_launch(self._h, blocks_per_sm, entries_per_thread, persistent))
+
     def time_kernel(self, name) -> float:
         """Milliseconds of one launch of a hot kernel (CUDA events on the handle stream)."""
         ms = C.c_float()
@@ -358,13 +364,16 @@ class Batch:
 
     @staticmethod
     def autotune(geoms, stream=None, **opts):
+        """Times the batch for a few launch shapes and leaves the geometries on the fastest;
+        returns ((blocks_per_sm, entries_per_thread, persistent), ms).  Run the batch with
+        blocks_per_sm=0 to keep that shape."""
         o = default_opts(**opts)
         arr = (C.c_void_p * len(geoms))(*[g._h.value for g in geoms])
-        best, ms = C.c_int(), C.c_double()
+        best, ms = (C.c_int * 3)(), C.c_double()
         st = geoms[0].stream if stream is None else stream
         _check(load().schur_batch_autotune(arr, len(geoms), C.byref(o), C.c_void_p(st),
                                            C.byref(best), C.byref(ms)))
-        return best.value, ms.value
+        return tuple(best), ms.value
 
     def run(self, allow_fail=False):
         n = len(self.geoms)

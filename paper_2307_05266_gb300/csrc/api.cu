@@ -48,7 +48,7 @@ cudaError_t alloc(Handle& H, T** p, size_t n) {
     return e;
 }
 
-void free_all(Handle& H) {
+void drop_graphs(Handle& H) {
     for (int k = 0; k < 4; ++k) {
         if (H.exec_solve[k]) cudaGraphExecDestroy(H.exec_solve[k]);
         if (H.graph_solve[k]) cudaGraphDestroy(H.graph_solve[k]);
@@ -57,14 +57,18 @@ void free_all(Handle& H) {
         H.exec_solve[k] = H.exec_full[k] = nullptr;
         H.graph_solve[k] = H.graph_full[k] = nullptr;
     }
-    if (H.done_ev) cudaEventDestroy(H.done_ev);
-    H.done_ev = nullptr;
     if (H.exec_recover) cudaGraphExecDestroy(H.exec_recover);
     if (H.graph_recover) cudaGraphDestroy(H.graph_recover);
     if (H.exec_solo) cudaGraphExecDestroy(H.exec_solo);
     if (H.graph_solo) cudaGraphDestroy(H.graph_solo);
     H.exec_recover = H.exec_solo = nullptr;
     H.graph_recover = H.graph_solo = nullptr;
+}
+
+void free_all(Handle& H) {
+    drop_graphs(H);
+    if (H.done_ev) cudaEventDestroy(H.done_ev);
+    H.done_ev = nullptr;
     void* bufs[] = {H.mask, H.flags, H.invdS, H.ax, H.ar, H.ap, H.aq, H.sx, H.sr, H.sp,
                     H.sq, H.op, H.orr, H.od, H.oq, H.og, H.u, H.partials, H.dctl,
                     H.cmpc, H.cmean, H.small_start, H.small_cells, H.ulist, H.flist,
@@ -320,6 +324,24 @@ int schur_set_error_internal(int code, const char* msg) { return set_error(code,
 namespace schur {
 
 Handle& handle_of(schur_geom_t g) { return g->H; }
+
+int set_launch_shape(Handle& H, int blocks_per_sm, int entries_per_thread, int persistent) {
+    if (blocks_per_sm < 1 || blocks_per_sm > 32 || entries_per_thread < 1 ||
+        entries_per_thread > 4096 || (persistent != 0 && persistent != 1))
+        return set_error(SCHUR_EINVAL, "blocks_per_sm must lie in [1, 32], entries_per_thread "
+                                       "in [1, 4096] and persistent_inner in {0, 1}");
+    if (H.pending) return set_error(SCHUR_ESTATE, "an asynchronous solve is in flight");
+    const int tb = std::min(kMaxBlocks, H.nsm * blocks_per_sm);
+    if (tb != H.target_blocks || entries_per_thread != H.min_per_thread ||
+        (persistent != 0) != H.persistent) {
+        cudaStreamSynchronize(H.stream);  // recorded graphs may still run
+        drop_graphs(H);
+        H.target_blocks = tb;
+        H.min_per_thread = entries_per_thread;
+        H.persistent = persistent != 0;
+    }
+    return SCHUR_OK;
+}
 
 int check_opts(const schur_opts& o) {
     if (o.precond != SCHUR_UZAWA && o.precond != SCHUR_SIMPLE)
@@ -785,6 +807,12 @@ int schur_solve_A(schur_geom_t G, const double* b, double* x, double tol, int ma
     const int st = call_status(c, c->solo.status);
     if (st != SCHUR_OK) set_error(st, status_text(H, "inner A solve did not converge"));
     return st;
+}
+
+int schur_set_launch(schur_geom_t G, int blocks_per_sm, int entries_per_thread,
+                     int persistent_inner) {
+    if (!G) return set_error(SCHUR_EINVAL, "null handle");
+    return set_launch_shape(G->H, blocks_per_sm, entries_per_thread, persistent_inner);
 }
 
 int schur_time_kernel(schur_geom_t G, int kernel, float* ms) {

@@ -17,7 +17,10 @@ struct Handle {
     Dev g{};
     cudaStream_t stream = nullptr;
     int nsm = 152;
-    int target_blocks = 1216;
+    int target_blocks = 1216;    // grid cap: blocks per SM of the launch shape x SMs
+    int min_per_thread = 1;      // grids also give every thread at least this many entries
+    bool persistent = true;      // inner solves: one cooperative loop kernel (else one graph
+                                 // node per phase inside a conditional while node)
 
     uint8_t* mask = nullptr;     // [ncell]
     uint8_t* flags = nullptr;    // [d][stride]
@@ -125,4 +128,6 @@ int download_ctl_async(Handle& H);
 void fill_solve_stats(Handle& H, int precision, schur_stats* stats);
 void fill_recover_stats(Handle& H, schur_stats* stats);
 Handle& handle_of(schur_geom_t g);
+// Set the launch shape of a handle's kernels and drop its recorded graphs.
+int set_launch_shape(Handle& H, int blocks_per_sm, int entries_per_thread, int persistent);
 }  // namespace schur

@@ -1288,12 +1288,14 @@ static int resident_blocks(const void* k) {
     return nb;
 }
 
-// Streaming grids: one block per kBlock entries, at most one wave of resident blocks
-// (nsm x min(blocks per SM of the launch shape, resident blocks of the kernel)), so
-// that the grid-stride loops end together instead of leaving a partial last wave.
+// Streaming grids: one block per kBlock x min_per_thread entries, at most one wave of
+// resident blocks (nsm x min(blocks per SM of the launch shape, resident blocks of the
+// kernel)), so that the grid-stride loops end together instead of leaving a partial last
+// wave (and the cooperative loop kernels always fit).
 template <class K>
 static inline dim3 sgrid(const Handle& H, long long n, K k) {
-    const long long nb = (n + kBlock - 1) / kBlock;
+    const long long per_block = (long long)kBlock * std::max(1, H.min_per_thread);
+    const long long nb = (n + per_block - 1) / per_block;
     const long long cap = std::min<long long>(H.target_blocks,
                                               (long long)H.nsm * resident_blocks((const void*)k));
     return dim3((unsigned)std::max<long long>(1, std::min(nb, cap)));
@@ -1342,11 +1344,26 @@ static void record_A_solve(Handle& H, Recorder& R, InnerA<T> v, CgState* st, int
                            const double* P, double cp, double cf, const double* bvec) {
     const Compact C = compact_of(H);
     const long long nu = H.n_u;
-    R.launch("cgA_init", k_cgA_init<T>, sgrid(H, nu, k_cgA_init<T>), sblock(), H.g, C, v.x, v.r, P, cp, cf,
-             bvec, H.dctl, st, H.partials, -1);
-    (void)s;
-    R.launch_coop("cgA_loop", k_cgA_loop<T>, sgrid(H, nu, k_cgA_loop<T>), sblock(), H.g, C, v.x,
-                  v.r, v.p, v.q, H.dctl, st, H.partials);
+    if (H.persistent) {
+        R.launch("cgA_init", k_cgA_init<T>, sgrid(H, nu, k_cgA_init<T>), sblock(), H.g, C, v.x, v.r,
+                 P, cp, cf, bvec, H.dctl, st, H.partials, -1);
+        R.launch_coop("cgA_loop", k_cgA_loop<T>, sgrid(H, nu, k_cgA_loop<T>), sblock(), H.g, C,
+                      v.x, v.r, v.p, v.q, H.dctl, st, H.partials);
+        return;
+    }
+    // one graph node per phase inside a conditional while node: many geometries that share
+    // the GPU interleave at phase granularity
+    R.launch("cgA_init", k_cgA_init<T>, sgrid(H, nu, k_cgA_init<T>), sblock(), H.g, C, v.x, v.r, P,
+             cp, cf, bvec, H.dctl, st, H.partials, s);
+    R.loop(s, [&H, C, v, st, s, nu](Recorder& B) {
+        B.launch("cgA_dir", k_cgA_dir<T>, sgrid(H, nu, k_cgA_dir<T>), sblock(), H.g, nu,
+                 (const uint8_t*)H.ufl, (const T*)v.r, v.p, H.dctl, (const CgState*)st);
+        B.launch("cgA_matvec", k_cgA_matvec<T>, sgrid(H, nu, k_cgA_matvec<T>), sblock(), H.g, C,
+                 (const T*)v.p, v.q, H.dctl, st, H.partials, s);
+        B.launch("cgA_update", k_cgA_update<T>, sgrid(H, nu, k_cgA_update<T>), sblock(), H.g, nu,
+                 (const uint8_t*)H.ufl, v.x, v.r, (const T*)v.p, (const T*)v.q, H.dctl, st,
+                 H.partials, s);
+    });
 }
 
 template <typename T>
@@ -1373,11 +1390,21 @@ static void record_S_solve(Handle& H, Recorder& R, InnerS<T> v, CgState* st, int
     record_comp_means<double>(H, R, H.orr, 1);
     R.launch("cgS_init", k_cgS_init<T>, sgrid(H, np, k_cgS_init<T>), sblock(), H.g, C, v.invd,
              (const int*)H.cmpc, (const double*)H.cmean, H.orr, v.x, v.r, H.dctl, st,
-             (const CgState*)&H.dctl->out, H.partials, -1);
-    (void)s;
-    R.launch_coop("cgS_loop", k_cgS_loop<T>, sgrid(H, np, k_cgS_loop<T>), sblock(), H.g, C,
-                  v.invd, v.diag, v.x, v.r, v.p, v.q, H.dctl, st, H.partials,
-                  (const int*)&H.dctl->out.skip_next);
+             (const CgState*)&H.dctl->out, H.partials, H.persistent ? -1 : s);
+    if (H.persistent) {
+        R.launch_coop("cgS_loop", k_cgS_loop<T>, sgrid(H, np, k_cgS_loop<T>), sblock(), H.g, C,
+                      v.invd, v.diag, v.x, v.r, v.p, v.q, H.dctl, st, H.partials,
+                      (const int*)&H.dctl->out.skip_next);
+    } else {
+        R.loop(s, [&H, C, v, st, s, np](Recorder& B) {
+            B.launch("cgS_dir", k_cgS_dir<T>, sgrid(H, np, k_cgS_dir<T>), sblock(), H.g, np, v.invd,
+                     (const T*)v.r, v.p, H.dctl, (const CgState*)st);
+            B.launch("cgS_matvec", k_cgS_matvec<T>, sgrid(H, np, k_cgS_matvec<T>), sblock(), H.g, C,
+                     v.diag, (const T*)v.p, v.q, H.dctl, st, H.partials, s);
+            B.launch("cgS_update", k_cgS_update<T>, sgrid(H, np, k_cgS_update<T>), sblock(), H.g, np,
+                     v.invd, v.x, v.r, (const T*)v.p, (const T*)v.q, H.dctl, st, H.partials, s);
+        });
+    }
     record_comp_means<T>(H, R, (const T*)v.x, 0);
 }
 

@@ -22,6 +22,12 @@
 
 using namespace schur;
 
+// Geometries that share the GPU (batch branches, served jobs) size their grids by work as
+// well: at least this many entries per thread, so that a small geometry takes a few SMs
+// and leaves the rest to the others (the inner loop kernels hold their SMs for a whole
+// inner solve).
+constexpr int kSharedEntriesPerThread = 16;
+
 // ------------------------------------------------------------------------------------
 // batch
 // ------------------------------------------------------------------------------------
@@ -51,8 +57,8 @@ extern "C" int schur_batch_create(schur_geom_t* geoms, int n, const schur_opts* 
     o.loop_mode = SCHUR_LOOP_GRAPH;
     int rc = check_opts(o);
     if (rc) return rc;
-    if (blocks_per_sm < 1 || blocks_per_sm > 32)
-        return schur_set_error_internal(SCHUR_EINVAL, "blocks_per_sm must lie in [1, 32]");
+    if (blocks_per_sm < 0 || blocks_per_sm > 32)
+        return schur_set_error_internal(SCHUR_EINVAL, "blocks_per_sm must lie in [0, 32]");
     schur_batch* b = new schur_batch();
     b->geoms.assign(geoms, geoms + n);
     b->opts = o;
@@ -75,8 +81,9 @@ extern "C" int schur_batch_create(schur_geom_t* geoms, int n, const schur_opts* 
             delete b;
             return schur_set_error_internal(SCHUR_ESTATE, "a geometry has an asynchronous solve in flight");
         }
-        H.target_blocks = std::min(kMaxBlocks, std::max(1, H.nsm * blocks_per_sm));
-        if ((rc = prepare_solve(H, o, 1))) {
+        if ((blocks_per_sm > 0 &&
+             (rc = set_launch_shape(H, blocks_per_sm, kSharedEntriesPerThread, 1))) ||
+            (rc = prepare_solve(H, o, 1))) {
             batch_free(b);
             delete b;
             return rc;
@@ -150,45 +157,52 @@ extern "C" void schur_batch_destroy(schur_batch_t b) {
     delete b;
 }
 
-// Time the whole batch for blocks_per_sm in {2, 4, 8, 16} (one untimed and one timed run
-// each) and return the fastest; the geometries keep that launch shape afterwards.
+// Launch shapes tried by the autotuner: {blocks_per_sm, entries_per_thread, persistent}.
+// Persistent inner loops make each solve faster but hold their SMs for a whole inner
+// solve; per-phase graph nodes let many geometries interleave.
+static const int kTuneShapes[][3] = {
+    {8, 1, 0}, {2, 1, 0}, {8, kSharedEntriesPerThread, 1}, {2, kSharedEntriesPerThread, 1},
+    {1, kSharedEntriesPerThread, 1}};
+
+// Time the whole batch for every shape of kTuneShapes (one untimed and one timed run
+// each) and keep the fastest on the geometries.
 extern "C" int schur_batch_autotune(schur_geom_t* geoms, int n, const schur_opts* opts,
-                                    void* stream, int* best_blocks_per_sm, double* best_ms) {
-    if (!best_blocks_per_sm) return schur_set_error_internal(SCHUR_EINVAL, "null output");
-    const int cand[] = {2, 4, 8, 16};
+                                    void* stream, int best_shape[3], double* best_ms) {
+    if (!best_shape || !geoms || n < 1)
+        return schur_set_error_internal(SCHUR_EINVAL, "bad autotune arguments");
     double best = 1e300;
-    int arg = 8;
+    int arg = 0;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return schur_set_error_internal(SCHUR_ECUDA, "event create");
-    for (int bps : cand) {
+    const int nshape = (int)(sizeof(kTuneShapes) / sizeof(kTuneShapes[0]));
+    int rc = SCHUR_OK;
+    for (int c = 0; c < nshape && rc == SCHUR_OK; ++c) {
+        const int* sh = kTuneShapes[c];
+        for (int i = 0; i < n && rc == SCHUR_OK; ++i)
+            rc = set_launch_shape(handle_of(geoms[i]), sh[0], sh[1], sh[2]);
         schur_batch_t b = nullptr;
-        int rc = schur_batch_create(geoms, n, opts, bps, stream, &b);
-        if (rc) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return rc;
-        }
+        if (rc == SCHUR_OK) rc = schur_batch_create(geoms, n, opts, 0, stream, &b);
+        if (rc != SCHUR_OK) break;
         schur_batch_run(b, nullptr, nullptr, nullptr);  // warm-up
         cudaEventRecord(e0, (cudaStream_t)stream);
-        rc = schur_batch_run(b, nullptr, nullptr, nullptr);
+        const int rr = schur_batch_run(b, nullptr, nullptr, nullptr);
         cudaEventRecord(e1, (cudaStream_t)stream);
         cudaEventSynchronize(e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         schur_batch_destroy(b);
-        if (rc == SCHUR_OK && ms < best) {
+        if (rr == SCHUR_OK && ms < best) {
             best = ms;
-            arg = bps;
+            arg = c;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    for (int i = 0; i < n; ++i) {
-        Handle& H = handle_of(geoms[i]);
-        H.target_blocks = std::min(kMaxBlocks, std::max(1, H.nsm * arg));
-    }
-    *best_blocks_per_sm = arg;
+    if (rc != SCHUR_OK) return rc;
+    const int* sh = kTuneShapes[arg];
+    for (int i = 0; i < n; ++i) set_launch_shape(handle_of(geoms[i]), sh[0], sh[1], sh[2]);
+    for (int k = 0; k < 3; ++k) best_shape[k] = sh[k];
     if (best_ms) *best_ms = best;
     return SCHUR_OK;
 }
@@ -228,20 +242,26 @@ struct schur_server {
     std::vector<schur_job_result> done;
     int64_t peak_used = 0;
     int peak_active = 0;
+    // launch shape of every job: per-phase graph nodes, so that the jobs in flight
+    // interleave at phase granularity (measured: higher capacity than persistent loops)
+    int shape[3] = {8, 1, 0};
 };
 
 static double now_s(const schur_server* s) {
     return std::chrono::duration<double>(Clock::now() - s->t0).count();
 }
 
-// Device bytes of one job, from the allocations schur_create_geometry and a solve make:
-// face space d * cells of flags, four FP64 inner vectors, the velocity and the work list;
-// cell space of mask, S-hat diagonal, four SIMPLE and five outer FP64 vectors, the
-// component ids and the fluid list; FP32 inner vectors in mixed precision.
+// Device bytes of one job, an upper bound from the allocations schur_create_geometry and
+// a solve make, counting every face as an unknown and every cell as fluid.  Per face
+// (d x cells): flags 1, velocity 8, work list 4, flag copy 1, four FP64 inner vectors 32,
+// neighbour table 8d (2d 4-byte entries).  Per cell: mask 1, S-hat inverse diagonal
+// (dense and compact) and diagonal 24, component id 4, cell list 4, five outer and four
+// SIMPLE FP64 vectors 72, neighbour table 8d, face codes 4.  Mixed precision adds four
+// FP32 vectors per face and five per cell.
 extern "C" int64_t schur_footprint_bytes(int ndim, const int64_t dims[3], int precision) {
     const int64_t nc = dims[0] * dims[1] * (ndim == 3 ? dims[2] : 1);
     const int64_t nf = (int64_t)ndim * ((nc + 63) / 64 * 64);
-    int64_t b = nf * (1 + 4 * 8 + 8 + 4) + nc * (1 + 8 + 4 * 8 + 5 * 8 + 4 + 4 + 4);
+    int64_t b = nf * (1 + 8 + 4 + 1 + 4 * 8 + 8 * ndim) + nc * (1 + 24 + 4 + 4 + 9 * 8 + 8 * ndim + 4);
     if (precision == SCHUR_MIXED) b += nf * 4 * 4 + nc * 5 * 4;
     return b + (4 << 20);
 }
@@ -345,6 +365,8 @@ extern "C" int schur_server_progress(schur_server_t s, int* n_active, int* n_pen
             rc = schur_set_error_internal(SCHUR_ECUDA, "stream create");
         if (rc == SCHUR_OK)
             rc = schur_create_geometry(j.mask.data(), j.ndim, j.dims, j.periodic, j.stream, &j.geom);
+        if (rc == SCHUR_OK)
+            rc = set_launch_shape(handle_of(j.geom), s->shape[0], s->shape[1], s->shape[2]);
         if (rc == SCHUR_OK) {
             double f[3] = {0.0, 0.0, 0.0};
             f[j.axis] = 1.0;

@@ -77,4 +77,5 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.schur_create_geometry(m, 3, dims1, per, None, ctypes.byref(out)) == binding.SCHUR_EINVAL
     assert b"extent" in lib.schur_last_error()
     assert lib.schur_solve(None, None, None) == binding.SCHUR_EINVAL
+    assert lib.schur_set_launch(None, 8, 1, 1) == binding.SCHUR_EINVAL
     lib.schur_destroy(None)

@@ -23,10 +23,12 @@ def _masks():
     return [synth.sphere_packing(n, a, b, phi, s) for n, a, b, phi, s in specs]
 
 
-def _alone(mask, axis, **opts):
+def _alone(mask, axis, launch=None, **opts):
     f = [0.0, 0.0, 0.0]
     f[axis] = 1.0
     with binding.Geometry(mask) as g:
+        if launch is not None:
+            g.set_launch(*launch)
         g.set_force(f)
         st = g.solve(**opts)
         rs = g.recover_velocity()
@@ -51,7 +53,9 @@ def test_async_equals_sync():
 def test_batch_equals_individual(precision):
     torch.cuda.set_device(0)
     masks = _masks()
-    refs = [_alone(m, 0, precond=binding.SIMPLE, precision=precision, tol=1e-8) for m in masks]
+    # a batch member runs with launch shape (blocks_per_sm, 16 entries per thread)
+    refs = [_alone(m, 0, launch=(8, 16, 1), precond=binding.SIMPLE, precision=precision,
+                   tol=1e-8) for m in masks]
     geoms = [binding.Geometry(m) for m in masks]
     b = binding.Batch(geoms, blocks_per_sm=8, precond=binding.SIMPLE, precision=precision,
                       tol=1e-8)
@@ -72,8 +76,8 @@ def test_batch_autotune_keeps_results():
     geoms = [binding.Geometry(m) for m in masks]
     best, ms = binding.Batch.autotune(geoms, precond=binding.UZAWA, precision=binding.MIXED,
                                       tol=1e-8)
-    assert best in (2, 4, 8, 16) and ms > 0
-    b = binding.Batch(geoms, blocks_per_sm=best, precond=binding.UZAWA,
+    assert len(best) == 3 and best[2] in (0, 1) and ms > 0
+    b = binding.Batch(geoms, blocks_per_sm=0, precond=binding.UZAWA,
                       precision=binding.MIXED, tol=1e-8)
     ss, rs, ks = b.run()
     for i, ref in enumerate(refs):
@@ -127,3 +131,24 @@ def test_server_admission_respects_budget():
     assert all(r["status"] == binding.SCHUR_OK for r in res)
     # waiting jobs start only after earlier ones free memory
     assert all(r["t_start"] >= r["t_submit"] for r in res)
+
+
+def test_launch_shape_changes_only_rounding():
+    """The launch shape (grid cap, entries per thread) changes the order of the floating-
+    point reductions only: results agree to rounding, and an equal shape repeats the bits."""
+    torch.cuda.set_device(0)
+    mask = _masks()[1]
+    out = []
+    with binding.Geometry(mask) as g:
+        g.set_force((1.0, 0.0, 0.0))
+        for shape in ((8, 1, 1), (2, 16, 1), (1, 64, 1), (8, 1, 0), (8, 1, 1)):
+            g.set_launch(*shape)
+            st = g.solve(precond=binding.SIMPLE, tol=1e-8)
+            g.recover_velocity()
+            out.append((st.outer_iters, g.permeability(0)))
+        with pytest.raises(RuntimeError):
+            g.set_launch(0, 1)
+    assert out[4] == out[0]
+    for it, k in out[1:4]:
+        assert abs(it - out[0][0]) <= 1
+        assert abs(k - out[0][1]) <= 1e-10 * abs(out[0][1])
