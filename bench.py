@@ -308,6 +308,19 @@ def serve_specs(n_req, max_edge, seed=7):
     return specs, axes, rng
 
 
+def job_rate(ms_local, units_per_rank, world, device):
+    """Whole-job rate of N replicas: every rank's units over the slowest rank's time (max
+    over ranks of the local milliseconds; an all-reduce when world > 1).  Returns
+    (units per second, max milliseconds)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return units_per_rank * world / (ms_max / 1e3), ms_max
+
+
 def time_kernels(binding, torch, mask_dev, reps):
     """Per-kernel timing on the headline workload: CUDA events around single launches on
     the geometry's stream, L2 flushed before every launch by reading a 512 MiB buffer
@@ -445,13 +458,7 @@ def gpu_arm(args):
             launches += n
         e1.record(stream)
         barrier()
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    solves = 2 * args.steps * world
-    value = solves / (ms_max / 1e3)
+    value, ms_max = job_rate(e0.elapsed_time(e1), 2 * args.steps, world, "cuda")
 
     # end to end: host mask in, permeabilities out
     barrier()
@@ -460,10 +467,7 @@ def gpu_arm(args):
         step(mask_np, None)
     e1.record(stream)
     barrier()
-    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = solves / (float(t.item()) / 1e3)
+    e2e_value, _ = job_rate(e0.elapsed_time(e1), 2 * args.steps, world, "cuda")
 
     per = {}
     for name, rows in rec.items():
