@@ -12,6 +12,11 @@
                   of Algorithm 1 and the unpreconditioned ||r_k||/||r_0|| used for the
                   2D study (Section 4.2.2).
 
+* ``lanczos_tridiagonal`` / ``lanczos_cond``  the condition-number estimate the paper
+                  computes "for free" from the outer CG coefficients (Section 4.2,
+                  Table 2): the Lanczos tridiagonal matrix that CG builds implicitly
+                  (Saad, Iterative Methods, Section 6.7.3) and its extreme eigenvalues.
+
 Iteration counts are the number of operator applications inside the loop.  A zero
 right-hand side returns the zero vector after 0 iterations.
 """
@@ -163,3 +168,36 @@ def schur_pcg(apply_S, g: np.ndarray, precond, tol: float, max_outer: int,
     out.inner_iters_A = it_A
     out.inner_iters_S = it_S
     return out
+
+
+def lanczos_tridiagonal(alphas, betas) -> np.ndarray:
+    """The m x m symmetric tridiagonal T_m of the Lanczos process that m steps of
+    (preconditioned) CG carry out implicitly, from the step lengths alpha_j and the
+    direction coefficients beta_j = rho_(j+1) / rho_j (Saad, Section 6.7.3):
+    T[j, j] = 1/alpha_j + beta_(j-1)/alpha_(j-1) (no second term for j = 0) and
+    T[j, j+1] = T[j+1, j] = sqrt(beta_j) / alpha_j.  Its eigenvalues (Ritz values)
+    approximate those of M^-1 S from the extremes inwards."""
+    a = np.asarray(alphas, dtype=np.float64)
+    b = np.asarray(betas, dtype=np.float64)
+    m = len(a)
+    if m == 0:
+        return np.zeros((0, 0))
+    T = np.zeros((m, m))
+    for j in range(m):
+        T[j, j] = 1.0 / a[j]
+        if j > 0:
+            T[j, j] += b[j - 1] / a[j - 1]
+        if j + 1 < m:
+            off = np.sqrt(b[j]) / a[j]
+            T[j, j + 1] = off
+            T[j + 1, j] = off
+    return T
+
+
+def lanczos_cond(alphas, betas):
+    """(lambda_min, lambda_max, lambda_max / lambda_min) of the Lanczos tridiagonal; a CG
+    run that stopped before forming beta of its last step uses the first len(betas) + 1
+    step lengths."""
+    m = min(len(alphas), len(betas) + 1)
+    w = np.linalg.eigvalsh(lanczos_tridiagonal(alphas[:m], betas[:m - 1]))
+    return float(w[0]), float(w[-1]), float(w[-1] / w[0])

@@ -396,3 +396,39 @@ def test_simple_solve_projects_onto_range():
     np.testing.assert_allclose(prob.S_simple @ res.x, r, atol=1e-9 * np.abs(r).max())
     means = np.bincount(prob.comp, weights=res.x) / prob.comp_size
     assert np.abs(means).max() < 1e-12 * max(1.0, np.abs(res.x).max())
+
+
+# ---- Lanczos condition estimate from CG coefficients (Section 4.2) ----------------
+def test_lanczos_tridiagonal_recovers_spectrum_of_preconditioned_matrix():
+    """CG run to completion on an SPD matrix with Jacobi M: the Ritz values of the
+    implicit Lanczos tridiagonal reach the extreme eigenvalues of M^-1 A (linear algebra,
+    independent of the Stokes code)."""
+    rng = np.random.default_rng(0)
+    n = 30
+    Q = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    A = (Q * np.geomspace(1.0, 1e3, n)) @ Q.T
+    minv = 1.0 / np.diag(A)
+    res = krylov.pcg(lambda x: A @ x, rng.standard_normal(n), minv, 1e-15, 200)
+    lmin, lmax, cond = krylov.lanczos_cond(res.alphas, res.betas)
+    s = np.sqrt(minv)
+    w = np.linalg.eigvalsh((s[:, None] * A) * s[None, :])
+    assert lmin == pytest.approx(w[0], rel=1e-10)
+    assert lmax == pytest.approx(w[-1], rel=1e-10)
+    assert cond == pytest.approx(w[-1] / w[0], rel=1e-10)
+
+
+@pytest.mark.parametrize("n_avg", [4, 8])
+def test_lanczos_cond_of_outer_cg_matches_dense(n_avg):
+    """The estimate from Algorithm 1's coefficients: cond(S) of CG-Uzawa equals the dense
+    effective condition number; the CG-SIMPLE estimate of cond(S-hat^-1 S) lies within a
+    few per cent below it (Ritz values lie inside the spectrum)."""
+    m = synth.square_array_2d(3, 14, n_avg, 2, seed=7)
+    prob = stokes.StokesProblem(m)
+    r = stokes.solve(m, (1.0, 0.0), stokes.Options(precond=stokes.UZAWA, tol=1e-10))
+    est = krylov.lanczos_cond(r["schur"].alphas, r["schur"].betas)
+    assert est[1] == pytest.approx(1.0, rel=1e-9)             # lambda_max(S) = 1
+    assert est[2] == pytest.approx(dense.effective_cond(dense.spectrum(prob)), rel=1e-5)
+    r = stokes.solve(m, (1.0, 0.0), stokes.Options(precond=stokes.SIMPLE, tol=1e-10))
+    est = krylov.lanczos_cond(r["schur"].alphas, r["schur"].betas)
+    ref = dense.effective_cond(dense.preconditioned_spectrum(prob))
+    assert 0.95 * ref <= est[2] <= ref * (1 + 1e-9)
