@@ -7,14 +7,15 @@ on "spheres128" (128^3 periodic overlapping spheres, radii U[4,8), porosity 0.40
 f = e_x).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--patterns mixed,batch,serve,tight|none]
+                    [--patterns mixed,batch,serve,tight,suite2d|none]
 
 Prints one JSON line.  value = Schur solves per second with the mask resident on the
 device; e2e = the same with the mask in host memory (H2D copy and permeability D2H inside
 the timed region).  After the timed region (N = 1 only) the line also reports the
 mixed-precision solves of the same workload, a batch of 64 uneven packings solved by one
-graph launch, a Poisson-arrival serving run with p50/p99 latency, and the tight 256^3
-packing (porosity 0.15) in mixed precision against FP64.  --impl reference
+graph launch, a Poisson-arrival serving run with p50/p99 latency, the tight 256^3
+packing (porosity 0.15) in mixed precision against FP64, and the paper's 2D square-array
+study (iterations, e#, Lanczos condition estimates beside the paper's Table 4).  --impl reference
 times the FP64 CPU oracle on a bounded sample of the same workload and scales it to whole
 solves with the oracle's own recorded iteration counts.
 """
@@ -536,6 +537,8 @@ def gpu_arm(args):
 
     if world == 1 and "mixed" in patterns:
         line["mixed_precision"] = mixed_pattern(binding, mask_dev, per, solve_kw)
+    if world == 1 and "suite2d" in patterns:
+        line["suite2d"] = suite2d_pattern(binding, torch)
     if pending is not None:
         bmasks, smasks, tmasks = pending[0].get(), pending[1].get(), pending[2].get()
         pool.close()
@@ -716,6 +719,53 @@ def tight_pattern(binding, torch, mask):
     return out
 
 
+# The paper's 2D study (Section 4.2.1-4.2.2, Tables 3-4): N x N = 7 x 7 randomly shifted
+# squares in cells of n_c = 50 pixels (n = 350), n_min = 2, n_avg in {4, ..., 12}; outer
+# CG to the unpreconditioned ||r||/||r_0|| < 1e-3, inner solves to 1e-13.  The paper's
+# own numbers (its CPU, its random shifts) are quoted beside ours as context.
+SUITE2D_PAPER = {
+    "n_avg": [4, 6, 8, 10, 12],
+    "uzawa_iters": [138, 98, 81, 61, 52], "simple_iters": [15, 22, 29, 35, 40],
+    "cond_S": [4.7e3, 2.3e3, 1.3e3, 7.7e2, 5.3e2],
+    "cond_simple_S": [3.4e1, 8.6e1, 1.6e2, 2.6e2, 3.4e2],
+    "uzawa_err_pct": [5.4e-5, 4.4e-5, 4.3e-5, 3.6e-5, 3.4e-5],
+    "simple_err_pct": [1.4e-6, 1.5e-6, 1.5e-6, 1.5e-6, 1.5e-6],
+    "uzawa_s": [6.5, 6.0, 5.8, 5.0, 4.7], "simple_s": [1.4, 2.4, 3.5, 4.6, 5.7],
+}
+
+
+def suite2d_pattern(binding, torch, seed=0):
+    """CG-Uzawa and CG-SIMPLE on the 2D square arrays: outer iterations, seconds, the
+    permeability error e# against a tight reference (CG-SIMPLE to 1e-10), and Lanczos
+    estimates of cond(S) and cond(S-hat^-1 S) from the reference-tolerance runs."""
+    from paper_2307_05266_gb300 import synth
+    rows = []
+    for n_avg in SUITE2D_PAPER["n_avg"]:
+        mask = synth.square_array_2d(7, 50, n_avg, 2, seed)
+        row = {"n_avg": n_avg, "porosity": float(mask.mean())}
+        with binding.Geometry(torch.from_numpy(mask).cuda()) as g:
+            g.set_force((1.0, 0.0))
+            g.solve(precond=binding.SIMPLE, tol=1e-10, tol_inner_A=1e-13, tol_inner_S=1e-13)
+            g.recover_velocity()
+            k_ref = g.permeability(0)
+            row["cond_simple_S_lanczos"] = g.cond_estimate()[2]
+            g.solve(precond=binding.UZAWA, tol=1e-10, tol_inner_A=1e-13)
+            row["cond_S_lanczos"] = g.cond_estimate()[2]
+            for name, pc in (("uzawa", binding.UZAWA), ("simple", binding.SIMPLE)):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st = g.solve(precond=pc, tol=1e-3, tol_inner_A=1e-13, tol_inner_S=1e-13)
+                g.recover_velocity()
+                k = g.permeability(0)
+                row[name] = {"iters": st.outer_iters, "s": time.perf_counter() - t0,
+                             "err_pct": 100.0 * abs(k - k_ref) / abs(k_ref),
+                             "inner_A": st.inner_iters_A, "inner_S": st.inner_iters_S}
+        rows.append(row)
+    return {"workload": "square arrays N=7, n_c=50, n_min=2, n=350, seed %d, f = e_x; "
+                        "outer tol 1e-3 (unpreconditioned), inner 1e-13, FP64" % seed,
+            "rows": rows, "paper_table4_context": SUITE2D_PAPER}
+
+
 import numpy as np  # noqa: E402  (used by the patterns)
 
 
@@ -725,7 +775,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--patterns", default="mixed,batch,serve,tight")
+    ap.add_argument("--patterns", default="mixed,batch,serve,tight,suite2d")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-max-edge", type=int, default=192)
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],

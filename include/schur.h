@@ -157,6 +157,35 @@ int schur_recover_velocity(schur_geom_t g, schur_stats* stats);
  * FP64.  Synchronises the stream.  SCHUR_ESTATE before any recovery. */
 int schur_permeability(schur_geom_t g, int axis, double* k_out);
 
+/* Diagonal of the permeability tensor (Section 2.3): for each axis a < ndim, a unit body
+ * force along a, schur_solve with *opts (NULL: defaults) and schur_recover_velocity on the
+ * same handle (flags, components, tables and graphs are shared), then k_out[a] = k_aa;
+ * k_out[a] = 0 for a >= ndim.  stats (may be NULL) receives ndim solve stats.  The force
+ * is left at the last axis.  Returns the worst status (k_out still written for the axes
+ * that converged).  Synchronises. */
+int schur_permeability_diag(schur_geom_t g, const schur_opts* opts, double k_out[3],
+                            schur_stats* stats);
+
+/* Per-iteration record of the last solve's outer loop (Algorithm 1; in mixed precision
+ * the flexible CG steps of all refinements): for outer iteration k < min(*n, cap) the
+ * step length alpha_k, the direction coefficient beta_k (NaN when the loop stopped
+ * before forming it), ||r_(k+1)|| / ||r_0|| (the recursive residual) and ||z_(k+1)|| /
+ * ||z_0|| (NaN when z was not formed).  *n = number of recorded iterations (at most
+ * min(max_outer, 131072)).  Any output array may be NULL.  Synchronises.
+ * SCHUR_ESTATE before any solve. */
+int schur_history(schur_geom_t g, int cap, double* alpha, double* beta, double* rel,
+                  double* relz, int* n);
+
+/* Condition-number estimate of the preconditioned Schur operator (S for Uzawa, S-hat^-1 S
+ * for SIMPLE) from the outer CG coefficients of the last FP64 solve, as in Section 4.2:
+ * the extreme eigenvalues of the Lanczos tridiagonal matrix T[j][j] = 1/alpha_j +
+ * beta_(j-1)/alpha_(j-1), T[j][j+1] = sqrt(beta_j)/alpha_j (Saad, Section 6.7.3), by
+ * Sturm-sequence bisection on the host.  The Ritz values lie inside the spectrum, so
+ * *cond <= the effective condition number; it converges to it as the iteration proceeds.
+ * SCHUR_ESTATE after a mixed-precision solve (flexible CG defines no Lanczos matrix) or a
+ * solve without outer iterations. */
+int schur_cond_estimate(schur_geom_t g, double* lambda_min, double* lambda_max, double* cond);
+
 /* Borrowed device pointer to a field (valid until the next solve/recover or destroy):
  * P (f64, cells), U (f64, faces), FLAGS (u8, faces), MASK (u8, cells), G (f64, cells). */
 int schur_get_field(schur_geom_t g, int which, void** dev_ptr, int64_t* elems, int* dtype);

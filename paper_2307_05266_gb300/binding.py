@@ -33,7 +33,7 @@ EXPORTED = [
     "schur_batch_destroy", "schur_footprint_bytes", "schur_server_create",
     "schur_server_submit", "schur_server_progress", "schur_server_take", "schur_server_info",
     "schur_server_destroy",
-    "schur_set_launch",
+    "schur_set_launch", "schur_permeability_diag", "schur_history", "schur_cond_estimate",
 ]
 KERNELS = {"cgA_dir": 0, "cgA_matvec": 1, "cgA_update": 2, "cgS_dir": 3, "cgS_matvec": 4,
            "cgS_update": 5, "cgA_dir_f32": 6, "cgA_matvec_f32": 7, "cgA_update_f32": 8,
@@ -111,6 +111,11 @@ def load(build_if_missing: bool = True):
         "schur_solve_A": (C.c_int, [vp, vp, vp, C.c_double, C.c_int, C.POINTER(C.c_int)]),
         "schur_time_kernel": (C.c_int, [vp, C.c_int, C.POINTER(C.c_float)]),
         "schur_set_launch": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
+        "schur_history": (C.c_int, [vp, C.c_int, vp, vp, vp, vp, C.POINTER(C.c_int)]),
+        "schur_cond_estimate": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                          C.POINTER(C.c_double)]),
+        "schur_permeability_diag": (C.c_int, [vp, C.POINTER(Opts), C.POINTER(C.c_double),
+                                              C.POINTER(Stats)]),
         "schur_permeability_noalloc": (C.c_int, [vp, vp, C.c_int, i64p, C.c_int64, vp, vp]),
         "schur_solve_async": (C.c_int, [vp, C.POINTER(Opts)]),
         "schur_query": (C.c_int, [vp, C.POINTER(C.c_int)]),
@@ -303,6 +308,33 @@ class Geometry:
         it = C.c_int()
         _check(load().schur_solve_A(self._h, _ptr(b), _ptr(x), tol, max_iter, C.byref(it)))
         return it.value
+
+    def permeability_diag(self, allow_fail=False, **kw):
+        """(k_xx, k_yy, k_zz) and the solve stats of each axis (schur_permeability_diag)."""
+        o = default_opts(**kw)
+        k = (C.c_double * 3)()
+        st = (Stats * 3)()
+        rc = load().schur_permeability_diag(self._h, C.byref(o), k, st)
+        _check(rc, (SCHUR_OK, SCHUR_ENOTCONV, SCHUR_EBREAKDOWN) if allow_fail else (SCHUR_OK,))
+        return tuple(k), list(st)[:self.info.ndim]
+
+    def history(self):
+        """Per-iteration record of the last solve: dict of numpy arrays alpha, beta, rel,
+        relz (schur_history)."""
+        import numpy as np
+        n = C.c_int()
+        _check(load().schur_history(self._h, 0, None, None, None, None, C.byref(n)))
+        out = {k: np.full(n.value, np.nan) for k in ("alpha", "beta", "rel", "relz")}
+        if n.value:
+            ptr = [out[k].ctypes.data_as(C.c_void_p) for k in ("alpha", "beta", "rel", "relz")]
+            _check(load().schur_history(self._h, n.value, *ptr, C.byref(n)))
+        return out
+
+    def cond_estimate(self):
+        """(lambda_min, lambda_max, cond) from the last FP64 solve's CG coefficients."""
+        lo, hi, c = C.c_double(), C.c_double(), C.c_double()
+        _check(load().schur_cond_estimate(self._h, C.byref(lo), C.byref(hi), C.byref(c)))
+        return lo.value, hi.value, c.value
 
     def set_launch(self, blocks_per_sm=8, entries_per_thread=1, persistent=1):
         """Launch shape of this geometry's kernels (see schur_set_launch)."""

@@ -36,7 +36,41 @@ int cuda_error(cudaError_t e, const char* what) {
     } while (0)
 
 constexpr int kHostSlotBase = 24;
-constexpr long long kMaxCompact = (1ll << 31) - (1ll << 24);  // host-driven loops reuse slots 24..31 on every call
+constexpr long long kMaxCompact = (1ll << 31) - (1ll << 24);
+constexpr int kHistMax = 1 << 17;  // outer iterations kept in the per-iteration record
+
+// Eigenvalues of the symmetric tridiagonal matrix (diagonal d[0..m), off-diagonal
+// e[0..m-1)) below x: the number of negative pivots of the LDL^T factorisation of T - x I
+// (Sturm sequence count).
+long long sturm_count(const std::vector<double>& d, const std::vector<double>& e, double x) {
+    long long cnt = 0;
+    double q = 1.0;
+    for (size_t i = 0; i < d.size(); ++i) {
+        const double off = i ? e[i - 1] * e[i - 1] : 0.0;
+        q = d[i] - x - (i ? off / q : 0.0);
+        if (q == 0.0) q = -1e-300;
+        if (q < 0.0) ++cnt;
+    }
+    return cnt;
+}
+
+// The k-th smallest eigenvalue (k = 0 .. m-1) of the tridiagonal matrix by bisection on
+// the Sturm count inside the Gershgorin interval.
+double tridiag_eig(const std::vector<double>& d, const std::vector<double>& e, long long k) {
+    const size_t m = d.size();
+    double lo = d[0], hi = d[0];
+    for (size_t i = 0; i < m; ++i) {
+        const double r = (i ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(e[i]) : 0.0);
+        lo = std::min(lo, d[i] - r);
+        hi = std::max(hi, d[i] + r);
+    }
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (sturm_count(d, e, mid) > k) hi = mid; else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}  // host-driven loops reuse slots 24..31 on every call
 
 template <class T>
 cudaError_t alloc(Handle& H, T** p, size_t n) {
@@ -74,7 +108,7 @@ void free_all(Handle& H) {
                     H.cmpc, H.cmean, H.small_start, H.small_cells, H.ulist, H.flist,
                     H.axf, H.arf, H.apf, H.aqf, H.sxf, H.srf, H.spf, H.sqf, H.invdSf,
                     H.ufl, H.fmask, H.fbase, H.cmask, H.cbase, H.invdSc, H.stage,
-                    H.nbA, H.nbS, H.codeS, H.dSc};
+                    H.nbA, H.nbS, H.codeS, H.dSc, H.hist};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (H.hctl) cudaFreeHost(H.hctl);
@@ -377,8 +411,23 @@ int prepare_solve(Handle& H, const schur_opts& o, int use_graph) {
         if (e == cudaErrorMemoryAllocation) return set_error(SCHUR_ENOMEM, "device allocation failed");
         if (e != cudaSuccess) return cuda_error(e, "mixed-precision buffers");
     }
+    // per-iteration record of the outer loop, NaN-filled (all bytes 0xff) before the call
+    const int need = std::min(std::max(o.max_outer, 1), kHistMax);
+    if (H.hist_cap < need) {
+        if (H.hist) cudaFree(H.hist);
+        H.hist = nullptr;
+        H.hist_cap = 0;
+        cudaError_t e = cudaMalloc((void**)&H.hist, (size_t)need * 4 * sizeof(double));
+        if (e == cudaErrorMemoryAllocation) return set_error(SCHUR_ENOMEM, "device allocation failed");
+        if (e != cudaSuccess) return cuda_error(e, "history buffer");
+        H.hist_cap = need;
+    }
+    CUDA_TRY(cudaMemsetAsync(H.hist, 0xff, (size_t)need * 4 * sizeof(double), H.stream),
+             "history reset");
     Ctl* c = H.hctl;
     reset_call(H, use_graph);
+    c->hist = H.hist;
+    c->hist_cap = need;
     c->precond = o.precond;
     c->stop_norm = o.stop_norm;
     c->inA.tol = o.tol_inner_A;
@@ -711,6 +760,88 @@ int schur_permeability(schur_geom_t G, int axis, double* k_out) {
     if (axis < 0 || axis >= H.g.d) return set_error(SCHUR_EINVAL, "axis out of range");
     if (!H.recovered) return set_error(SCHUR_ESTATE, "permeability needs recover_velocity first");
     *k_out = H.hctl->perm[axis];
+    return SCHUR_OK;
+}
+
+int schur_permeability_diag(schur_geom_t G, const schur_opts* opts, double k_out[3],
+                            schur_stats* stats) {
+    if (!G || !k_out) return set_error(SCHUR_EINVAL, "null argument");
+    Handle& H = G->H;
+    if (H.pending) return set_error(SCHUR_ESTATE, "an asynchronous solve is in flight");
+    int worst = SCHUR_OK;
+    std::string msg;
+    for (int a = 0; a < 3; ++a) k_out[a] = 0.0;
+    for (int a = 0; a < H.g.d; ++a) {
+        double f[3] = {0.0, 0.0, 0.0};
+        f[a] = 1.0;
+        int rc = schur_set_force(G, f);
+        if (rc == SCHUR_OK || rc == SCHUR_ENOTCONV) {
+            rc = schur_solve(G, opts, stats ? &stats[a] : nullptr);
+            if (rc == SCHUR_OK || rc == SCHUR_ENOTCONV) {
+                const int rr = schur_recover_velocity(G, nullptr);
+                if (rr != SCHUR_OK && rc == SCHUR_OK) rc = rr;
+                if (H.recovered) k_out[a] = H.hctl->perm[a];
+            }
+        }
+        if (rc != SCHUR_OK) {
+            if (worst == SCHUR_OK || rc == SCHUR_ECUDA || rc == SCHUR_ENOMEM) {
+                worst = rc;
+                msg = schur_last_error();
+            }
+            if (rc != SCHUR_ENOTCONV && rc != SCHUR_EBREAKDOWN) break;
+        }
+    }
+    if (worst != SCHUR_OK) set_error(worst, msg.c_str());
+    return worst;
+}
+
+int schur_history(schur_geom_t G, int cap, double* alpha, double* beta, double* rel,
+                  double* relz, int* n) {
+    if (!G || !n || cap < 0) return set_error(SCHUR_EINVAL, "bad history arguments");
+    Handle& H = G->H;
+    if (H.pending) return set_error(SCHUR_ESTATE, "an asynchronous solve is in flight");
+    if (!H.solved) return set_error(SCHUR_ESTATE, "history needs a schur_solve first");
+    const int m = std::min({H.hctl->out.iter, H.hist_cap, cap});
+    *n = std::min(H.hctl->out.iter, H.hist_cap);
+    if (m <= 0) return SCHUR_OK;
+    std::vector<double> h((size_t)m * 4);
+    CUDA_TRY(cudaMemcpyAsync(h.data(), H.hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                             H.stream), "history download");
+    CUDA_TRY(cudaStreamSynchronize(H.stream), "stream synchronize");
+    for (int k = 0; k < m; ++k) {
+        if (alpha) alpha[k] = h[4 * k + 0];
+        if (beta) beta[k] = h[4 * k + 1];
+        if (rel) rel[k] = h[4 * k + 2];
+        if (relz) relz[k] = h[4 * k + 3];
+    }
+    return SCHUR_OK;
+}
+
+int schur_cond_estimate(schur_geom_t G, double* lmin, double* lmax, double* cond) {
+    if (!G || !lmin || !lmax || !cond) return set_error(SCHUR_EINVAL, "null argument");
+    Handle& H = G->H;
+    if (H.pending) return set_error(SCHUR_ESTATE, "an asynchronous solve is in flight");
+    if (!H.solved || H.last_precision != SCHUR_FP64)
+        return set_error(SCHUR_ESTATE, "the estimate needs the coefficients of an FP64 solve "
+                                       "(flexible CG coefficients define no Lanczos matrix)");
+    const int m = std::min(H.hctl->out.iter, H.hist_cap);
+    if (m < 1) return set_error(SCHUR_ESTATE, "the last solve made no outer iteration");
+    std::vector<double> a(m), b(m);
+    int n = 0;
+    int rc = schur_history(G, m, a.data(), b.data(), nullptr, nullptr, &n);
+    if (rc) return rc;
+    // Lanczos tridiagonal of CG (Saad, Section 6.7.3): T[j][j] = 1/a_j + b_(j-1)/a_(j-1),
+    // T[j][j+1] = sqrt(b_j)/a_j
+    std::vector<double> d(m), e(m > 1 ? m - 1 : 0);
+    for (int j = 0; j < m; ++j) {
+        if (!(a[j] > 0.0) || (j + 1 < m && !(b[j] >= 0.0)))
+            return set_error(SCHUR_ESTATE, "the recorded CG coefficients are not usable");
+        d[j] = 1.0 / a[j] + (j ? b[j - 1] / a[j - 1] : 0.0);
+        if (j + 1 < m) e[j] = std::sqrt(b[j]) / a[j];
+    }
+    *lmin = tridiag_eig(d, e, 0);
+    *lmax = tridiag_eig(d, e, m - 1);
+    *cond = *lmax / *lmin;
     return SCHUR_OK;
 }
 

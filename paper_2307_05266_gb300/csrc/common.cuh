@@ -118,9 +118,22 @@ struct Ctl {
     // when a wait ran past its limit
     unsigned int bar_count;
     unsigned int bar_err;
+    // per-iteration record of the outer iteration (4 doubles per iteration: alpha, beta,
+    // ||r||/||r_0||, ||z||/||z_0||; NaN where a value was not formed); null: no record
+    double* hist;
+    int hist_cap;
+    int pad2;
 };
 
 inline long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+// Slots of the per-iteration record.
+enum HistSlot : int { H_ALPHA = 0, H_BETA = 1, H_REL = 2, H_RELZ = 3 };
+
+// Record value v of outer iteration k (0-based) when it fits the record.
+__device__ __forceinline__ void hist_put(Ctl* ctl, int k, int slot, double v) {
+    if (ctl->hist && k >= 0 && k < ctl->hist_cap) ctl->hist[4 * (size_t)k + slot] = v;
+}
 
 // ---- device helpers ---------------------------------------------------------------
 

@@ -63,6 +63,8 @@ struct Handle {
     double* stage = nullptr;     // [d][stride] staging of schur_solve_A's right-hand side
     long long n_u = 0, n_p = 0;
     double* partials = nullptr;  // reduction scratch
+    double* hist = nullptr;      // [hist_cap][4] per-iteration record of the outer loop
+    int hist_cap = 0;
     Ctl* dctl = nullptr;         // device control block
     Ctl* hctl = nullptr;         // pinned host shadow
 

@@ -965,6 +965,7 @@ __global__ void k_outer_div(Dev g, Compact C, const uint8_t* __restrict__ mask,
             set_cond(ctl, slot, 0u);
         } else {
             o->alpha = o->rho / dq;
+            hist_put(ctl, o->iter, H_ALPHA, o->alpha);
         }
     }
 }
@@ -989,6 +990,7 @@ __global__ void k_outer_update(Dev g, double* __restrict__ pv, double* __restric
         o->total += 1;
         const double rel = sqrt(v[0] / o->rr0);
         o->rel = rel;
+        hist_put(ctl, o->iter - 1, H_REL, rel);
         unsigned cont = 1u;
         if (ctl->bar_err) {
             o->status = ST_BARRIER;  // an inner solve failed: stop
@@ -1000,6 +1002,7 @@ __global__ void k_outer_update(Dev g, double* __restrict__ pv, double* __restric
         } else if (ctl->precond == 0) {
             // Uzawa: z = r
             o->relz = sqrt(v[0] / o->zz0);
+            hist_put(ctl, o->iter - 1, H_RELZ, o->relz);
             if (ctl->stop_norm == 1 && o->relz < o->tol) {
                 o->status = ST_OK;
                 cont = 0u;
@@ -1012,6 +1015,7 @@ __global__ void k_outer_update(Dev g, double* __restrict__ pv, double* __restric
             } else {
                 o->beta = v[0] / o->rho;
                 o->rho = v[0];
+                hist_put(ctl, o->iter - 1, H_BETA, o->beta);
             }
         } else {
             o->cap = (o->iter >= o->max_iter);
@@ -1047,6 +1051,7 @@ __global__ void k_outer_dots(Dev g, Compact C, const int* __restrict__ cmpc,
     }
     if (reduce_last_block<2>(v, partials, &ctl->ticket) && is_thread0()) {
         o->relz = sqrt(v[1] / o->zz0);
+        hist_put(ctl, o->iter - 1, H_RELZ, o->relz);
         unsigned cont = 1u;
         if (ctl->stop_norm == 1 && o->relz < o->tol) {
             o->status = ST_OK;
@@ -1057,6 +1062,7 @@ __global__ void k_outer_dots(Dev g, Compact C, const int* __restrict__ cmpc,
         } else {
             o->beta = v[0] / o->rho;
             o->rho = v[0];
+            hist_put(ctl, o->iter - 1, H_BETA, o->beta);
         }
         if (!cont) {
             o->done = 1;
@@ -1142,6 +1148,7 @@ __global__ void k_fcg_div(Dev g, Compact C, const uint8_t* __restrict__ mask,
             set_cond(ctl, slot_ref, 0u);
         } else {
             o->alpha = v[1] / dq;
+            hist_put(ctl, o->iter, H_ALPHA, o->alpha);
             ctl->mix.dq = dq;
         }
     }
@@ -1168,6 +1175,7 @@ __global__ void k_fcg_update(Dev g, double* __restrict__ pv, double* __restrict_
         o->iter += 1;
         o->total += 1;
         m.step_iter += 1;
+        hist_put(ctl, o->iter - 1, H_REL, sqrt(v[0] / o->rr0));
         const double f2 = m.factor * m.factor;
         const int done = (v[0] <= f2 * m.rr_step0) || (v[0] < o->tol * o->tol * o->rr0) ||
                          (m.step_iter >= m.step_max) || (o->iter >= o->max_iter) ||
@@ -1197,6 +1205,7 @@ __global__ void k_fcg_dots(Dev g, Compact C, const int* __restrict__ cmpc,
     }
     if (reduce_last_block<1>(v, partials, &ctl->ticket) && is_thread0())
         o->beta = -v[0] / ctl->mix.dq;
+        hist_put(ctl, o->iter - 1, H_BETA, o->beta);
 }
 
 // True residual r = g - B u with u = A^-1 B^T p from an FP64 inner solve; decides whether

@@ -290,3 +290,54 @@ def test_mixed_zero_rhs_and_loop_modes(cuda):
             out.append((st.outer_iters, st.refinements, st.inner_iters_A_f32,
                         g.field(binding.FIELD_P).clone()))
     assert out[0][:3] == out[1][:3] and torch.equal(out[0][3], out[1][3])
+
+
+@pytest.mark.parametrize("name", ["spheres_ragged", "rand2d_closed_y"])
+def test_permeability_diagonal_matches_oracle(cuda, name):
+    """k_xx, k_yy (, k_zz) from three solves sharing one handle (Section 2.3)."""
+    mask, per, geo, g = _pair(name)
+    k, stats = g.permeability_diag(precond=binding.SIMPLE, tol=1e-9)
+    assert len(stats) == geo.d and all(s.status == binding.SCHUR_OK for s in stats)
+    for a in range(geo.d):
+        f = [0.0, 0.0, 0.0][:geo.d]
+        f[a] = 1.0
+        ref = stokes.solve(mask, tuple(f), stokes.Options(precond=stokes.SIMPLE, tol=1e-9), per)
+        assert abs(k[a] - ref["k"][a]) <= 1e-8 * abs(ref["k"][a]) + 1e-9 * geo.h ** 2
+    assert all(v == 0.0 for v in k[geo.d:])
+    g.close()
+
+
+@pytest.mark.parametrize("precond", [binding.UZAWA, binding.SIMPLE])
+def test_history_and_lanczos_cond_match_oracle(cuda, precond):
+    """Per-iteration residuals and the Lanczos condition estimate from the outer CG
+    coefficients (Section 4.2) against the oracle's own run and the dense spectrum."""
+    from oracle import dense
+    mask = synth.square_array_2d(3, 14, 4, 2, seed=7)
+    ref = stokes.solve(mask, (1.0, 0.0), stokes.Options(precond=precond, tol=1e-10))
+    rs = ref["schur"]
+    with binding.Geometry(mask) as g:
+        g.set_force((1.0, 0.0))
+        st = g.solve(precond=precond, tol=1e-10)
+        h = g.history()
+        lo, hi, cond = g.cond_estimate()
+    n = st.outer_iters
+    assert abs(n - rs.outer_iters) <= 2 and len(h["rel"]) == n
+    m = min(n, rs.outer_iters, 10)
+    np.testing.assert_allclose(h["rel"][:m], rs.history[1:m + 1], rtol=1e-6)
+    np.testing.assert_allclose(h["alpha"][:m], rs.alphas[:m], rtol=1e-6)
+    assert np.isnan(h["beta"][n - 1]) and np.all(np.isfinite(h["beta"][:n - 1]))
+    ref_est = krylov.lanczos_cond(rs.alphas, rs.betas)
+    assert cond == pytest.approx(ref_est[2], rel=1e-5)
+    prob = ref["problem"]
+    w = dense.spectrum(prob) if precond == binding.UZAWA else dense.preconditioned_spectrum(prob)
+    assert cond <= dense.effective_cond(w) * (1 + 1e-8)
+
+
+def test_cond_estimate_refuses_mixed_precision(cuda):
+    mask = synth.square_array_2d(2, 10, 4, 2, seed=1)
+    with binding.Geometry(mask) as g:
+        g.set_force((1.0, 0.0))
+        g.solve(precond=binding.UZAWA, precision=binding.MIXED, tol=1e-8)
+        assert len(g.history()["rel"]) > 0
+        with pytest.raises(binding.SchurError):
+            g.cond_estimate()
