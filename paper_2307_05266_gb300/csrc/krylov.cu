@@ -323,6 +323,8 @@ __global__ void k_cgA_init(Dev g, Compact C, T* __restrict__ xv, T* __restrict__
 // Entries per thread and step of the stencil phases (independent gathers in flight).
 template <typename T> struct MvU { static constexpr int v = 4; };
 template <> struct MvU<double> { static constexpr int v = 2; };
+// ... and in the persistent loop kernel, where register pressure sets the occupancy.
+template <typename T> struct LoopMvU { static constexpr int v = 2; };
 
 // Per-block copies of the ghost-count tables in shared memory: a lookup is one indexed
 // shared load (no select chain, and nothing for the compiler to keep in registers across
@@ -368,13 +370,12 @@ __device__ __forceinline__ void phaseA_dir(const Tabs<T>& t, uint32_t n, const u
 
 // q = A' p; returns this thread's part of p.q.  The neighbour indices come from the table
 // (coalesced rows); missing neighbours point at the zero entry p[n_u].
-template <typename T>
+template <typename T, int U = MvU<T>::v>
 __device__ __forceinline__ T phaseA_matvec(const Tabs<T>& t, const Dev& g, const Compact& C,
                                            const T* __restrict__ pv, T* __restrict__ qv) {
     T acc = (T)0;
     const uint32_t n = (uint32_t)C.n_u;
     const int ne = 2 * g.d;
-    constexpr int U = MvU<T>::v;
     WARP_STREAM_BEGIN_U(n, U)
         uint32_t nb[U][6];
         int gh[U];
@@ -527,14 +528,13 @@ __device__ __forceinline__ void phaseS_dir(uint32_t n, const T* __restrict__ inv
 // diag(S-hat) p_c minus the weighted neighbour sum; FP32 sums the weighted differences
 // (p_c - p_nb), which vanish exactly on constants.  Closed faces point at the zero entry
 // p[n_p] with weight 0.
-template <typename T>
+template <typename T, int U = MvU<T>::v>
 __device__ __forceinline__ T phaseS_matvec(const Tabs<T>& t, const Dev& g, const Compact& C,
                                            const T* __restrict__ dS, const T* __restrict__ pv,
                                            T* __restrict__ qv) {
     T acc = (T)0;
     const uint32_t n = (uint32_t)C.n_p;
     const int ne = 2 * g.d;
-    constexpr int U = MvU<T>::v;
     WARP_STREAM_BEGIN_U(n, U)
         uint32_t nb[U][6], code[U];
         T pc[U], dg[U];
@@ -739,8 +739,11 @@ __device__ __forceinline__ void cg_loop(const Dev& g, const Compact& C, const T*
             Cl.nbS = opaque(C.nbS);
             Cl.codeS = opaque(C.codeS);
             Cl.ufl = opaque(C.ufl);
-            if constexpr (kS) v1[0] = (double)phaseS_matvec<T>(t, g, Cl, opaque(dS), opaque(pv), opaque(qv));
-            else v1[0] = (double)phaseA_matvec<T>(t, g, Cl, opaque(pv), opaque(qv));
+            constexpr int U = LoopMvU<T>::v;
+            if constexpr (kS)
+                v1[0] = (double)phaseS_matvec<T, U>(t, g, Cl, opaque(dS), opaque(pv), opaque(qv));
+            else
+                v1[0] = (double)phaseA_matvec<T, U>(t, g, Cl, opaque(pv), opaque(qv));
         }
         if (!(ok = grid_sum<1>(v1, P1, ctl, target))) break;
         if (threadIdx.x == 0) {
@@ -769,10 +772,10 @@ __device__ __forceinline__ void cg_loop(const Dev& g, const Compact& C, const T*
     }
 }
 
-// Minimum resident blocks per SM asked of the loop kernels: 3 for FP64 (pipe-bound, the
-// phases fit in 85 registers), 2 for FP32 (a lower bound spills the stencil's gathers).
-template <typename T> struct LoopMinBlocks { static constexpr int v = 2; };
-template <> struct LoopMinBlocks<double> { static constexpr int v = 3; };
+// Minimum resident blocks per SM asked of the loop kernels (3: the fused phases fit in 85
+// registers without spills; the stencil phase of the loop kernel gathers 2 entries per
+// thread and step in both precisions for that).
+template <typename T> struct LoopMinBlocks { static constexpr int v = 3; };
 
 // aux: unused for A; invd (Jacobi weights of S-hat) for S.  dS: diagonal of S-hat (read by
 // the FP64 S matvec).
@@ -1311,6 +1314,28 @@ static inline dim3 sgrid(const Handle& H, long long n, K k) {
 }
 static inline dim3 sblock() { return dim3(kBlock); }
 
+// Grids of the persistent loop kernels.  In the single-solve shape (one entry per thread
+// at least) a loop grid gives every thread kLoopMinPerThread entries but keeps one block
+// per SM when the problem has that many rows: mid-size inner solves run faster on fewer,
+// fuller blocks (cheaper barriers), small ones need the SMs for latency.  Shapes made for
+// sharing the GPU keep their own entries per thread.
+constexpr int kLoopMinPerThread = 4;
+template <class K>
+static inline dim3 lgrid(const Handle& H, long long n, K k) {
+    const long long cap = std::min<long long>(H.target_blocks,
+                                              (long long)H.nsm * resident_blocks((const void*)k));
+    const long long rows = (n + kBlock - 1) / kBlock;
+    long long nb;
+    if (H.min_per_thread > 1) {
+        const long long per_block = (long long)kBlock * H.min_per_thread;
+        nb = (n + per_block - 1) / per_block;
+    } else {
+        const long long per_block = (long long)kBlock * kLoopMinPerThread;
+        nb = std::max((n + per_block - 1) / per_block, std::min<long long>(H.nsm, rows));
+    }
+    return dim3((unsigned)std::max<long long>(1, std::min(nb, cap)));
+}
+
 static Compact compact_of(const Handle& H) {
     Compact C;
     C.ulist = H.ulist;
@@ -1356,7 +1381,7 @@ static void record_A_solve(Handle& H, Recorder& R, InnerA<T> v, CgState* st, int
     if (H.persistent) {
         R.launch("cgA_init", k_cgA_init<T>, sgrid(H, nu, k_cgA_init<T>), sblock(), H.g, C, v.x, v.r,
                  P, cp, cf, bvec, H.dctl, st, H.partials, -1);
-        R.launch_coop("cgA_loop", k_cgA_loop<T>, sgrid(H, nu, k_cgA_loop<T>), sblock(), H.g, C,
+        R.launch_coop("cgA_loop", k_cgA_loop<T>, lgrid(H, nu, k_cgA_loop<T>), sblock(), H.g, C,
                       v.x, v.r, v.p, v.q, H.dctl, st, H.partials);
         return;
     }
@@ -1401,7 +1426,7 @@ static void record_S_solve(Handle& H, Recorder& R, InnerS<T> v, CgState* st, int
              (const int*)H.cmpc, (const double*)H.cmean, H.orr, v.x, v.r, H.dctl, st,
              (const CgState*)&H.dctl->out, H.partials, H.persistent ? -1 : s);
     if (H.persistent) {
-        R.launch_coop("cgS_loop", k_cgS_loop<T>, sgrid(H, np, k_cgS_loop<T>), sblock(), H.g, C,
+        R.launch_coop("cgS_loop", k_cgS_loop<T>, lgrid(H, np, k_cgS_loop<T>), sblock(), H.g, C,
                       v.invd, v.diag, v.x, v.r, v.p, v.q, H.dctl, st, H.partials,
                       (const int*)&H.dctl->out.skip_next);
     } else {
@@ -1570,14 +1595,14 @@ static cudaError_t time_loop_t(Handle& H, bool simple, InnerA<T> a, InnerS<T> sv
     if (!simple) {
         void* args[] = {(void*)&H.g, (void*)&C, (void*)&a.x, (void*)&a.r, (void*)&a.p, (void*)&a.q,
                         (void*)&ctl, (void*)&st, (void*)&H.partials};
-        e = cudaLaunchCooperativeKernel((const void*)k_cgA_loop<T>, sgrid(H, H.n_u, k_cgA_loop<T>), b,
+        e = cudaLaunchCooperativeKernel((const void*)k_cgA_loop<T>, lgrid(H, H.n_u, k_cgA_loop<T>), b,
                                         args, 0, H.stream);
     } else {
         const int* gate = nullptr;
         void* args[] = {(void*)&H.g, (void*)&C, (void*)&sv.invd, (void*)&sv.diag, (void*)&sv.x,
                         (void*)&sv.r, (void*)&sv.p, (void*)&sv.q, (void*)&ctl, (void*)&st,
                         (void*)&H.partials, (void*)&gate};
-        e = cudaLaunchCooperativeKernel((const void*)k_cgS_loop<T>, sgrid(H, H.n_p, k_cgS_loop<T>), b,
+        e = cudaLaunchCooperativeKernel((const void*)k_cgS_loop<T>, lgrid(H, H.n_p, k_cgS_loop<T>), b,
                                         args, 0, H.stream);
     }
     if (e != cudaSuccess) return e;
