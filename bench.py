@@ -85,8 +85,8 @@ def kernel_model(name, nu, npf, d, loop_iters=20):
 # hot kernels on this workload from one ncu capture (cold cache) of the kernel sources
 # whose SHA-256 is given; reported as null once the sources differ.
 NCU_TRAFFIC = {
-    "sources_sha256": "a91de65beb8e2857ce05a5be40727db145f17857e282eacded912c8b24b56103",
-    "bytes": {"cgA_dir": 38441984, "cgA_matvec": 77139968, "cgA_update": 75935744, "cgS_dir": 20133632, "cgS_matvec": 36966912, "cgS_update": 33583104, "cgA_dir_f32": 20353536, "cgA_matvec_f32": 66861568, "cgA_update_f32": 38469888, "cgS_dir_f32": 10069248, "cgS_matvec_f32": 26868480, "cgS_update_f32": 16808448},
+    "sources_sha256": "07fbf1462793852d5f5af90e2fee451d46fd49380757fcd98619c74bbd2194ab",
+    "bytes": {"cgA_dir": 38443816, "cgA_matvec": 76970064, "cgA_update": 75882200, "cgS_dir": 20134000, "cgS_matvec": 36991000, "cgS_update": 33583000, "cgA_dir_f32": 20354000, "cgA_matvec_f32": 66932392, "cgA_update_f32": 38472000, "cgS_dir_f32": 10069000, "cgS_matvec_f32": 26864000, "cgS_update_f32": 16809000, "cgA_loop": 2045924616, "cgS_loop": 66799240, "cgA_loop_f32": 596482448, "cgS_loop_f32": 37517680},
 }
 
 
