@@ -240,9 +240,10 @@ __device__ __forceinline__ bool reduce_last_block(double (&v)[K], double* partia
 // ---- grid barrier of a cooperative launch ------------------------------------------
 
 // Polls of one barrier wait before it gives up: the first kBarrierBusy polls spin, the
-// rest sleep >= 128 ns each, so the limit is well over half a second, far beyond any
-// legal wait (microseconds).
-constexpr unsigned kBarrierSpins = 1u << 22;
+// rest sleep >= 128 ns each (a poll takes about 0.6 us in all), so the limit is about ten
+// seconds: far beyond a wait between co-resident blocks (microseconds), and long enough
+// for blocks that only become resident when another stream's kernel ends.
+constexpr unsigned kBarrierSpins = 1u << 24;
 constexpr unsigned kBarrierBusy = 1u << 10;
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
