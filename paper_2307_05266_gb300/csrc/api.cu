@@ -514,6 +514,7 @@ const char* schur_last_error(void) { return g_last_error.c_str(); }
 
 int schur_create_geometry(const uint8_t* mask, int ndim, const int64_t dims[3],
                           const int periodic[3], void* stream, schur_geom_t* out) {
+    NvtxRange nvtx_("schur_create_geometry");
     if (!out) return set_error(SCHUR_EINVAL, "out is NULL");
     *out = nullptr;
     if (!mask || !dims || !periodic) return set_error(SCHUR_EINVAL, "mask, dims or periodic is NULL");
@@ -644,6 +645,7 @@ int schur_set_force(schur_geom_t G, const double f[3]) {
 }
 
 int schur_solve(schur_geom_t G, const schur_opts* opts, schur_stats* stats) {
+    NvtxRange nvtx_("schur_solve");
     if (!G) return set_error(SCHUR_EINVAL, "null handle");
     schur_opts o;
     if (opts) o = *opts; else schur_opts_default(&o);
@@ -676,6 +678,7 @@ int schur_solve(schur_geom_t G, const schur_opts* opts, schur_stats* stats) {
 }
 
 int schur_recover_velocity(schur_geom_t G, schur_stats* stats) {
+    NvtxRange nvtx_("schur_recover_velocity");
     if (!G) return set_error(SCHUR_EINVAL, "null handle");
     Handle& H = G->H;
     if (H.pending) return set_error(SCHUR_ESTATE, "an asynchronous solve is in flight");
@@ -704,6 +707,7 @@ int schur_recover_velocity(schur_geom_t G, schur_stats* stats) {
 }
 
 int schur_solve_async(schur_geom_t G, const schur_opts* opts) {
+    NvtxRange nvtx_("schur_solve_async");
     if (!G) return set_error(SCHUR_EINVAL, "null handle");
     schur_opts o;
     if (opts) o = *opts; else schur_opts_default(&o);
@@ -765,6 +769,7 @@ int schur_permeability(schur_geom_t G, int axis, double* k_out) {
 
 int schur_permeability_diag(schur_geom_t G, const schur_opts* opts, double k_out[3],
                             schur_stats* stats) {
+    NvtxRange nvtx_("schur_permeability_diag");
     if (!G || !k_out) return set_error(SCHUR_EINVAL, "null argument");
     Handle& H = G->H;
     if (H.pending) return set_error(SCHUR_ESTATE, "an asynchronous solve is in flight");
@@ -910,6 +915,7 @@ int schur_apply_simple(schur_geom_t G, const double* p, double* q) {
 
 int schur_solve_A(schur_geom_t G, const double* b, double* x, double tol, int max_iter,
                   int* iters) {
+    NvtxRange nvtx_("schur_solve_A");
     if (!G || !b || !x) return set_error(SCHUR_EINVAL, "null argument");
     if (!(tol > 0) || max_iter < 1) return set_error(SCHUR_EINVAL, "tol must be > 0, max_iter >= 1");
     Handle& H = G->H;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <utility>
@@ -11,6 +12,15 @@
 #include "common.cuh"
 
 namespace schur {
+
+// NVTX range over one library call (shows the call in nsys/ncu timelines; a no-op when no
+// tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Device buffers and graphs of one geometry (the object behind schur_geom_t).
 struct Handle {

@@ -114,6 +114,7 @@ extern "C" int schur_batch_create(schur_geom_t* geoms, int n, const schur_opts* 
 // be NULL) receives 3 permeabilities per geometry.
 extern "C" int schur_batch_run(schur_batch_t b, schur_stats* solve_stats,
                                schur_stats* recover_stats, double* k_out) {
+    NvtxRange nvtx_("schur_batch_run");
     if (!b) return schur_set_error_internal(SCHUR_EINVAL, "null batch");
     int rc;
     for (schur_geom_t g : b->geoms) {
@@ -339,6 +340,7 @@ static void finish_job(schur_server* s, Job& j, int status, const schur_stats* s
 
 // Admit what fits, collect what finished.  Never blocks on the GPU.
 extern "C" int schur_server_progress(schur_server_t s, int* n_active, int* n_pending) {
+    NvtxRange nvtx_("schur_server_progress");
     if (!s) return schur_set_error_internal(SCHUR_EINVAL, "null server");
     // completions
     for (size_t i = 0; i < s->active.size();) {

@@ -7,6 +7,7 @@ import re
 import subprocess
 import tempfile
 
+import numpy as np
 import pytest
 
 from paper_2307_05266_gb300 import _build, binding
@@ -79,3 +80,21 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.schur_solve(None, None, None) == binding.SCHUR_EINVAL
     assert lib.schur_set_launch(None, 8, 1, 1) == binding.SCHUR_EINVAL
     lib.schur_destroy(None)
+
+
+def test_footprint_bound_grows_with_size_and_precision(lib):
+    fp = [binding.footprint_bytes((n, n, n)) for n in (16, 32, 64)]
+    assert fp[0] < fp[1] < fp[2]
+    assert binding.footprint_bytes((32, 32, 32), binding.MIXED) > fp[1]
+    # an upper bound on what a 64^3 geometry can allocate: per cell at least the dense
+    # FP64 outer vectors and the velocity (5 + 3 doubles) and the mask
+    assert fp[2] >= 64 ** 3 * (8 * 8 + 1)
+
+
+def test_server_rejects_job_larger_than_budget_without_gpu(lib):
+    """Host-side admission check (no device work happens before progress())."""
+    srv = binding.Server(1 << 20, max_active=2)
+    with pytest.raises(binding.SchurError) as e:
+        srv.submit(np.ones((64, 64, 64), np.uint8))
+    assert e.value.code == binding.SCHUR_ENOMEM
+    srv.close()

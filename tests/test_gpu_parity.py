@@ -341,3 +341,28 @@ def test_cond_estimate_refuses_mixed_precision(cuda):
         assert len(g.history()["rel"]) > 0
         with pytest.raises(binding.SchurError):
             g.cond_estimate()
+
+
+def test_invariants_and_host_side_faults(cuda):
+    """Values off the unknowns stay exactly zero; a non-finite force is rejected; a flow
+    axis blocked by a solid plane has zero permeability."""
+    mask = synth.sphere_packing((20, 18, 22), 2.0, 4.0, 0.45, seed=4)
+    with binding.Geometry(mask) as g:
+        with pytest.raises(binding.SchurError) as e:
+            g.set_force((float("nan"), 0.0, 0.0))
+        assert e.value.code == binding.SCHUR_EINVAL
+        g.set_force((0.0, 1.0, 0.0))
+        g.solve(precond=binding.SIMPLE, tol=1e-9)
+        g.recover_velocity()
+        flags = g.field(binding.FIELD_FLAGS).cpu().numpy()
+        u = g.field(binding.FIELD_U).cpu().numpy()
+        p = g.field(binding.FIELD_P).cpu().numpy()
+        m = g.field(binding.FIELD_MASK).cpu().numpy()
+        assert np.all(u[(flags & 1) == 0] == 0.0)
+        assert np.all(p[m == 0] == 0.0)
+    blocked = np.ones((12, 10, 16), np.uint8)
+    blocked[:, :, 7] = 0                       # a solid plane x = 7 blocks the x axis
+    with binding.Geometry(blocked) as g:
+        k, _ = g.permeability_diag(precond=binding.SIMPLE, tol=1e-10)
+        assert k[1] > 0 and k[2] > 0
+        assert abs(k[0]) <= 1e-9 * k[1]
