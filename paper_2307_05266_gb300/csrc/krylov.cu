@@ -693,8 +693,8 @@ __device__ __forceinline__ bool grid_sum(double (&v)[K], double* part, Ctl* ctl,
 }
 
 // Hides a value from the optimiser for one loop iteration, so that addresses derived
-// from it are recomputed in each phase instead of being kept in registers across all
-// phases of the loop kernel (which would cut its occupancy to two blocks per SM).
+// from it are recomputed in each phase rather than kept live across the other phases of
+// the loop kernel (the loop kernel is held to 85 registers by its launch bounds).
 template <class P>
 __device__ __forceinline__ P* opaque(P* p) {
     asm volatile("" : "+l"(p));
