@@ -640,9 +640,9 @@ def serve_pattern(binding, torch, masks, axes, rng, args):
     """Poisson-arrival serving at 80 % of the measured closed-loop capacity."""
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.6 * free)
-    # Uzawa needs thousands of outer iterations on the tightest requests (porosity ~0.1):
-    # the stagnation of Section 4.1 that motivates SIMPLE; the cap is raised accordingly
-    opts = dict(precond=binding.UZAWA, precision=binding.MIXED, tol=1e-8, max_outer=20000)
+    # per-request preconditioner: SIMPLE below 0.25 porosity, where Uzawa needs thousands of
+    # outer iterations (the stagnation of Section 4 that motivates SIMPLE), Uzawa otherwise
+    opts = dict(precond=binding.PRECOND_AUTO, precision=binding.MIXED, tol=1e-8, max_outer=20000)
 
     def run(arrivals, max_active):
         srv = binding.Server(budget, max_active=max_active, **opts)
@@ -673,7 +673,9 @@ def serve_pattern(binding, torch, masks, axes, rng, args):
     res, wall, info = run(arrivals, 16)
     lat = [r["t_done"] - r["t_submit"] for r in res]
     return {"requests": len(masks), "edges": [int(round(m.size ** (1 / 3))) for m in masks],
-            "precond": "uzawa", "precision": "mixed", "arrival_rate_per_s": rate,
+            "precond": "auto: simple below porosity %.2f, else uzawa" % binding.AUTO_SIMPLE_BELOW,
+            "precision": "mixed", "arrival_rate_per_s": rate,
+            "preconds": ["simple" if r["precond"] == binding.SIMPLE else "uzawa" for r in res],
             "capacity_per_s": capacity, "p50_s": pct(lat, 0.5), "p99_s": pct(lat, 0.99),
             "solves_per_s": len(res) / max(r["t_done"] for r in res),
             "peak_active": info["peak_active"], "peak_bytes": info["peak_bytes"],

@@ -53,6 +53,11 @@ extern "C" {
 #define SCHUR_ESTATE      6   /* call out of order (e.g. recover before solve) */
 
 enum { SCHUR_UZAWA = 0, SCHUR_SIMPLE = 1 };
+/* Server only (schur_server_create): choose per job, SIMPLE when the job's fluid fraction
+ * is below SCHUR_AUTO_SIMPLE_BELOW (tight geometries, where Uzawa stagnates: Section 4),
+ * Uzawa otherwise. */
+enum { SCHUR_PRECOND_AUTO = 2 };
+#define SCHUR_AUTO_SIMPLE_BELOW 0.25
 enum { SCHUR_STOP_UNPRECOND = 0, SCHUR_STOP_PRECOND = 1 };
 enum { SCHUR_FP64 = 0, SCHUR_MIXED = 1 };
 enum { SCHUR_LOOP_GRAPH = 0, SCHUR_LOOP_HOST = 1 };
@@ -281,8 +286,9 @@ void schur_batch_destroy(schur_batch_t b);
  * budget and fewer than max_active run, launches each on its own stream (geometry +
  * asynchronous solve + recovery, launch shape (8, 1, 0) of schur_set_launch: per-phase
  * graph nodes, so that the jobs in flight interleave), and collects finished ones without
- * blocking;
- * schur_server_take returns finished results.  Times are seconds since creation. */
+ * blocking; schur_server_take returns finished results.  opts->precond may be
+ * SCHUR_PRECOND_AUTO (a per-job choice from the host mask's fluid fraction).  Times are
+ * seconds since creation. */
 typedef struct {
     int64_t id;
     int status;
@@ -291,6 +297,8 @@ typedef struct {
     double k;                    /* permeability along the job's axis */
     double t_submit, t_start, t_done;
     int64_t bytes;               /* footprint charged to the budget */
+    int precond;                 /* preconditioner the job ran with */
+    int pad;
 } schur_job_result;
 
 int64_t schur_footprint_bytes(int ndim, const int64_t dims[3], int precision);

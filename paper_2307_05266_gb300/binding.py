@@ -18,6 +18,8 @@ from . import _build
 SCHUR_OK, SCHUR_EINVAL, SCHUR_ENOMEM, SCHUR_ENOTCONV = 0, 1, 2, 3
 SCHUR_EBREAKDOWN, SCHUR_ECUDA, SCHUR_ESTATE = 4, 5, 6
 UZAWA, SIMPLE = 0, 1
+PRECOND_AUTO = 2          # server only: SIMPLE below AUTO_SIMPLE_BELOW fluid fraction
+AUTO_SIMPLE_BELOW = 0.25
 STOP_UNPRECOND, STOP_PRECOND = 0, 1
 FP64, MIXED = 0, 1
 LOOP_GRAPH, LOOP_HOST = 0, 1
@@ -60,16 +62,17 @@ class Stats(C.Structure):
                 ("inner_iters_S_f32", C.c_longlong), ("refinements", C.c_int)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
 class JobResult(C.Structure):
     _fields_ = [("id", C.c_int64), ("status", C.c_int), ("outer_iters", C.c_int),
                 ("inner_iters", C.c_int64), ("k", C.c_double), ("t_submit", C.c_double),
-                ("t_start", C.c_double), ("t_done", C.c_double), ("bytes", C.c_int64)]
+                ("t_start", C.c_double), ("t_done", C.c_double), ("bytes", C.c_int64),
+                ("precond", C.c_int), ("pad", C.c_int)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
 class GeomInfo(C.Structure):

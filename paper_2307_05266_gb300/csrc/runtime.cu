@@ -223,6 +223,7 @@ struct Job {
     int64_t dims[3];
     int periodic[3];
     int axis;
+    int precond = SCHUR_UZAWA;
     int64_t bytes;
     double t_submit, t_start = 0, t_done = 0;
     schur_geom_t geom = nullptr;
@@ -274,7 +275,9 @@ extern "C" int schur_server_create(const schur_opts* opts, int64_t mem_budget_by
     schur_opts o;
     if (opts) o = *opts; else schur_opts_default(&o);
     o.loop_mode = SCHUR_LOOP_GRAPH;
-    int rc = check_opts(o);
+    schur_opts chk = o;
+    if (chk.precond == SCHUR_PRECOND_AUTO) chk.precond = SCHUR_SIMPLE;
+    int rc = check_opts(chk);
     if (rc) return rc;
     schur_server* s = new schur_server();
     s->opts = o;
@@ -303,6 +306,11 @@ extern "C" int schur_server_submit(schur_server_t s, const uint8_t* host_mask, i
     const int64_t nc = j.dims[0] * j.dims[1] * j.dims[2];
     j.mask.assign(host_mask, host_mask + nc);
     j.axis = axis;
+    j.precond = s->opts.precond;
+    if (j.precond == SCHUR_PRECOND_AUTO) {
+        const int64_t fluid = std::count(j.mask.begin(), j.mask.end(), (uint8_t)1);
+        j.precond = (double)fluid < SCHUR_AUTO_SIMPLE_BELOW * (double)nc ? SCHUR_SIMPLE : SCHUR_UZAWA;
+    }
     j.bytes = schur_footprint_bytes(ndim, j.dims, s->opts.precision);
     if (j.bytes > s->budget) return schur_set_error_internal(SCHUR_ENOMEM, "job larger than the memory budget");
     j.t_submit = now_s(s);
@@ -320,6 +328,7 @@ static void finish_job(schur_server* s, Job& j, int status, const schur_stats* s
     r.t_start = j.t_start;
     r.t_done = now_s(s);
     r.bytes = j.bytes;
+    r.precond = j.precond;
     if (j.geom) {
         double k = 0.0;
         if (status == SCHUR_OK || status == SCHUR_ENOTCONV) schur_permeability(j.geom, j.axis, &k);
@@ -374,7 +383,11 @@ extern "C" int schur_server_progress(schur_server_t s, int* n_active, int* n_pen
             f[j.axis] = 1.0;
             rc = schur_set_force(j.geom, f);
         }
-        if (rc == SCHUR_OK) rc = schur_solve_async(j.geom, &s->opts);
+        if (rc == SCHUR_OK) {
+            schur_opts o = s->opts;
+            o.precond = j.precond;
+            rc = schur_solve_async(j.geom, &o);
+        }
         j.mask.clear();
         j.mask.shrink_to_fit();
         if (rc != SCHUR_OK) {

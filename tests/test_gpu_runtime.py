@@ -152,3 +152,18 @@ def test_launch_shape_changes_only_rounding():
     for it, k in out[1:4]:
         assert abs(it - out[0][0]) <= 1
         assert abs(k - out[0][1]) <= 1e-10 * abs(out[0][1])
+
+
+def test_server_auto_preconditioner_by_porosity():
+    """SCHUR_PRECOND_AUTO: SIMPLE for tight jobs (fluid fraction below 0.25), Uzawa otherwise;
+    each result matches the same job solved alone with that preconditioner."""
+    torch.cuda.set_device(0)
+    masks = [synth.sphere_packing(24, 2.0, 3.0, 0.15, 8), synth.sphere_packing(24, 2.0, 4.0, 0.45, 9)]
+    res, _ = _serve(masks, [0, 0], 1 << 36, 4, precond=binding.PRECOND_AUTO,
+                    precision=binding.MIXED, tol=1e-8)
+    want = [binding.SIMPLE if m.mean() < binding.AUTO_SIMPLE_BELOW else binding.UZAWA for m in masks]
+    assert want == [binding.SIMPLE, binding.UZAWA]
+    for m, r, pc in zip(masks, res, want):
+        assert r["status"] == binding.SCHUR_OK and r["precond"] == pc
+        ref = _alone(m, 0, precond=pc, precision=binding.MIXED, tol=1e-8)
+        assert abs(r["k"] - ref[2]) <= 1e-6 * abs(ref[2])
