@@ -595,8 +595,9 @@ def mixed_pattern(binding, mask_dev, per, solve_kw):
 
 def batch_pattern(binding, torch, masks, stream):
     """64 uneven packings: one graph launch for all (autotuned launch shape) against the
-    same 64 solved one after another, mixed precision; FP64 sequential on the first 8."""
-    opts = dict(precond=binding.UZAWA, precision=binding.MIXED, tol=1e-8)
+    same 64 solved one after another, mixed precision, preconditioner chosen per geometry
+    (SIMPLE below 0.25 porosity); FP64 sequential on the first 8."""
+    opts = dict(precond=binding.PRECOND_AUTO, precision=binding.MIXED, tol=1e-8)
     geoms = [binding.Geometry(torch.from_numpy(m).cuda()) for m in masks]
     best, tune_ms = binding.Batch.autotune(geoms[:8], **opts)
     for g in geoms[8:]:
@@ -626,7 +627,9 @@ def batch_pattern(binding, torch, masks, stream):
     for g in geoms:
         g.close()
     return {"n_geometries": len(masks), "edges": sorted({m.shape[0] for m in masks}),
-            "cells_total": int(sum(cells)), "precond": "uzawa", "precision": "mixed",
+            "cells_total": int(sum(cells)),
+            "precond": "auto: simple below porosity %.2f, else uzawa" % binding.AUTO_SIMPLE_BELOW,
+            "precision": "mixed",
             "autotuned_shape": {"blocks_per_sm": best[0], "entries_per_thread": best[1],
                                 "persistent_inner": best[2]}, "batch_s": t_batch,
             "batch_solves_per_s": len(masks) / t_batch,

@@ -53,9 +53,9 @@ extern "C" {
 #define SCHUR_ESTATE      6   /* call out of order (e.g. recover before solve) */
 
 enum { SCHUR_UZAWA = 0, SCHUR_SIMPLE = 1 };
-/* Server only (schur_server_create): choose per job, SIMPLE when the job's fluid fraction
- * is below SCHUR_AUTO_SIMPLE_BELOW (tight geometries, where Uzawa stagnates: Section 4),
- * Uzawa otherwise. */
+/* Choose per geometry: SIMPLE when its fluid fraction is below SCHUR_AUTO_SIMPLE_BELOW
+ * (tight geometries, where Uzawa stagnates: Section 4), Uzawa otherwise.  Accepted by every
+ * call that takes schur_opts. */
 enum { SCHUR_PRECOND_AUTO = 2 };
 #define SCHUR_AUTO_SIMPLE_BELOW 0.25
 enum { SCHUR_STOP_UNPRECOND = 0, SCHUR_STOP_PRECOND = 1 };
@@ -74,7 +74,7 @@ typedef struct schur_server* schur_server_t;
  * max_inner 20000; mixed precision: tol_inner_f32 1e-5, refine_factor 1e-3,
  * max_refine 30, step_max 1000. */
 typedef struct {
-    int precond;        /* SCHUR_UZAWA | SCHUR_SIMPLE (eq. schur_uzawa_prec)                */
+    int precond;        /* SCHUR_UZAWA | SCHUR_SIMPLE (eq. schur_uzawa_prec) | _PRECOND_AUTO  */
     int stop_norm;      /* SCHUR_STOP_UNPRECOND: ||r_k||/||r_0|| < tol (Section 4.2.2);
                            SCHUR_STOP_PRECOND: ||z_k||/||z_0|| < tol (Algorithm 1)          */
     int precision;      /* SCHUR_FP64: everything in FP64 (Algorithm 1 as in the paper);

@@ -377,9 +377,17 @@ int set_launch_shape(Handle& H, int blocks_per_sm, int entries_per_thread, int p
     return SCHUR_OK;
 }
 
+schur_opts resolve_precond(const Handle& H, schur_opts o) {
+    if (o.precond == SCHUR_PRECOND_AUTO)
+        o.precond = (double)H.n_p < SCHUR_AUTO_SIMPLE_BELOW * (double)H.g.ncell ? SCHUR_SIMPLE
+                                                                               : SCHUR_UZAWA;
+    return o;
+}
+
 int check_opts(const schur_opts& o) {
-    if (o.precond != SCHUR_UZAWA && o.precond != SCHUR_SIMPLE)
-        return set_error(SCHUR_EINVAL, "precond must be SCHUR_UZAWA or SCHUR_SIMPLE");
+    if (o.precond != SCHUR_UZAWA && o.precond != SCHUR_SIMPLE && o.precond != SCHUR_PRECOND_AUTO)
+        return set_error(SCHUR_EINVAL, "precond must be SCHUR_UZAWA, SCHUR_SIMPLE or "
+                                       "SCHUR_PRECOND_AUTO");
     if (o.stop_norm != SCHUR_STOP_UNPRECOND && o.stop_norm != SCHUR_STOP_PRECOND)
         return set_error(SCHUR_EINVAL, "bad stop_norm");
     if (o.precision != SCHUR_FP64 && o.precision != SCHUR_MIXED)
@@ -399,7 +407,8 @@ int check_opts(const schur_opts& o) {
 
 // Allocate what the options need and write them into the host control block (the
 // recovery's inner solve uses the same tolerance and cap as the solve's A solves).
-int prepare_solve(Handle& H, const schur_opts& o, int use_graph) {
+int prepare_solve(Handle& H, const schur_opts& opts, int use_graph) {
+    const schur_opts o = resolve_precond(H, opts);  // the control block holds 0 or 1
     if (o.precision == SCHUR_MIXED && !H.axf) {
         // FP32 inner-solve buffers, allocated on the first mixed-precision solve
         const size_t nu = (size_t)std::max(H.n_u, 1ll), np = (size_t)std::max(H.n_p, 1ll);
@@ -653,6 +662,7 @@ int schur_solve(schur_geom_t G, const schur_opts* opts, schur_stats* stats) {
     if (H.pending) return set_error(SCHUR_ESTATE, "an asynchronous solve is in flight");
     int rc = check_opts(o);
     if (rc) return rc;
+    o = resolve_precond(H, o);
     if ((rc = prepare_solve(H, o, o.loop_mode == SCHUR_LOOP_GRAPH))) return rc;
     const int gi = o.precision * 2 + o.precond;
     if (o.loop_mode == SCHUR_LOOP_GRAPH) {
@@ -716,6 +726,7 @@ int schur_solve_async(schur_geom_t G, const schur_opts* opts) {
     if (H.pending) return set_error(SCHUR_ESTATE, "an asynchronous solve is in flight");
     int rc = check_opts(o);
     if (rc) return rc;
+    o = resolve_precond(H, o);
     if ((rc = prepare_solve(H, o, 1))) return rc;
     const int gi = o.precision * 2 + o.precond;
     rc = build_graph(H, &H.graph_full[gi], &H.exec_full[gi],

@@ -134,6 +134,8 @@ int schur_set_error_internal(int code, const char* msg);
 // paths.
 namespace schur {
 int check_opts(const schur_opts& o);
+// SCHUR_PRECOND_AUTO resolved for this geometry (SIMPLE below the fluid-fraction threshold).
+schur_opts resolve_precond(const Handle& H, schur_opts o);
 int prepare_solve(Handle& H, const schur_opts& o, int use_graph);
 int upload_ctl(Handle& H);
 int download_ctl_async(Handle& H);

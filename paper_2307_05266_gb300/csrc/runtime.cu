@@ -32,6 +32,7 @@ constexpr int kSharedEntriesPerThread = 16;
 // batch
 // ------------------------------------------------------------------------------------
 
+
 struct schur_batch {
     std::vector<schur_geom_t> geoms;
     schur_opts opts{};
@@ -83,14 +84,14 @@ extern "C" int schur_batch_create(schur_geom_t* geoms, int n, const schur_opts* 
         }
         if ((blocks_per_sm > 0 &&
              (rc = set_launch_shape(H, blocks_per_sm, kSharedEntriesPerThread, 1))) ||
-            (rc = prepare_solve(H, o, 1))) {
+            (rc = prepare_solve(H, resolve_precond(H, o), 1))) {
             batch_free(b);
             delete b;
             return rc;
         }
         const size_t before = H.handles.size();
         Recorder R(b->graph, H.dctl, &H.next_slot, &H.handles);  // branch from the graph root
-        record_solve_recover(H, R, o.precond, o.precision);
+        record_solve_recover(H, R, resolve_precond(H, o).precond, o.precision);
         if (!R.ok()) {
             std::string msg = "batch recording: " + R.where();
             batch_free(b);
@@ -275,9 +276,7 @@ extern "C" int schur_server_create(const schur_opts* opts, int64_t mem_budget_by
     schur_opts o;
     if (opts) o = *opts; else schur_opts_default(&o);
     o.loop_mode = SCHUR_LOOP_GRAPH;
-    schur_opts chk = o;
-    if (chk.precond == SCHUR_PRECOND_AUTO) chk.precond = SCHUR_SIMPLE;
-    int rc = check_opts(chk);
+    int rc = check_opts(o);
     if (rc) return rc;
     schur_server* s = new schur_server();
     s->opts = o;

@@ -167,3 +167,20 @@ def test_server_auto_preconditioner_by_porosity():
         assert r["status"] == binding.SCHUR_OK and r["precond"] == pc
         ref = _alone(m, 0, precond=pc, precision=binding.MIXED, tol=1e-8)
         assert abs(r["k"] - ref[2]) <= 1e-6 * abs(ref[2])
+
+
+def test_batch_auto_preconditioner_matches_individual():
+    torch.cuda.set_device(0)
+    masks = [synth.sphere_packing(24, 2.0, 3.0, 0.15, 8), synth.sphere_packing(24, 2.0, 4.0, 0.45, 9)]
+    want = [binding.SIMPLE, binding.UZAWA]
+    refs = [_alone(m, 0, launch=(8, 16, 1), precond=pc, precision=binding.MIXED, tol=1e-8)
+            for m, pc in zip(masks, want)]
+    geoms = [binding.Geometry(m) for m in masks]
+    b = binding.Batch(geoms, blocks_per_sm=8, precond=binding.PRECOND_AUTO,
+                      precision=binding.MIXED, tol=1e-8)
+    ss, rs, ks = b.run()
+    for s_, ref, k in zip(ss, refs, ks):
+        assert s_.outer_iters == ref[0] and k[0] == ref[2]
+    b.close()
+    for g in geoms:
+        g.close()
