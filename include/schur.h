@@ -95,7 +95,9 @@ typedef struct {
 } schur_opts;
 
 typedef struct {
-    int status;                  /* SCHUR_OK, SCHUR_ENOTCONV or SCHUR_EBREAKDOWN          */
+    int status;                  /* SCHUR_OK, SCHUR_ENOTCONV, SCHUR_EBREAKDOWN, or
+                                    SCHUR_ECUDA when an inner-solve grid barrier wait ran
+                                    past its limit (the results are then meaningless)      */
     int outer_iters;             /* S applications in Algorithm 1                          */
     int zero_rhs;                /* 1 when g vanished to rounding and p = 0 was returned   */
     int inner_status;            /* worst status of the inner solves                       */
