@@ -71,7 +71,7 @@ typedef struct schur_server* schur_server_t;
 
 /* Solver options.  Defaults (schur_opts_default): SIMPLE, unpreconditioned stop,
  * FP64, graph loop, tol 1e-8, tol_inner_A = tol_inner_S = 1e-12, max_outer 2000,
- * max_inner 20000; mixed precision: tol_inner_f32 1e-5, refine_factor 1e-3,
+ * max_inner 20000; mixed precision: tol_inner_f32 1e-4, refine_factor 1e-3,
  * max_refine 30, step_max 1000. */
 typedef struct {
     int precond;        /* SCHUR_UZAWA | SCHUR_SIMPLE (eq. schur_uzawa_prec) | _PRECOND_AUTO  */
@@ -88,7 +88,7 @@ typedef struct {
     double tol;         /* outer relative tolerance eps_S                                   */
     double tol_inner_A; /* inner tolerance eps_A: ||M^-1 r||/||M^-1 r_0|| (Section 3.2)     */
     double tol_inner_S; /* inner tolerance eps_S-hat for the SIMPLE solve (Section 3.2)     */
-    double tol_inner_f32;  /* MIXED: tolerance of the FP32 inner solves (default 1e-5)      */
+    double tol_inner_f32;  /* MIXED: tolerance of the FP32 inner solves (default 1e-4)      */
     double refine_factor;  /* MIXED: residual reduction of one refinement step (1e-3)       */
     int max_refine;        /* MIXED: cap on refinement steps (true residuals) (30)          */
     int step_max;          /* MIXED: cap on FCG iterations in one step (1000)               */

@@ -513,7 +513,7 @@ void schur_opts_default(schur_opts* o) {
     o->tol = 1e-8;
     o->tol_inner_A = 1e-12;
     o->tol_inner_S = 1e-12;
-    o->tol_inner_f32 = 1e-5;
+    o->tol_inner_f32 = 1e-4;
     o->refine_factor = 1e-3;
     o->max_refine = 30;
     o->step_max = 1000;
