@@ -94,9 +94,6 @@ struct Handle {
 
     double force[3] = {1.0, 0.0, 0.0};
     bool solved = false, recovered = false;
-    int last_precond = 1, last_stop = 0;
-    double last_tolA = 1e-12;
-    int last_max_inner = 20000;
     int last_loop = 0;
     int last_precision = 0;
     long long bytes = 0;
