@@ -193,6 +193,13 @@ int schur_history(schur_geom_t g, int cap, double* alpha, double* beta, double* 
  * solve without outer iterations. */
 int schur_cond_estimate(schur_geom_t g, double* lambda_min, double* lambda_max, double* cond);
 
+/* The host computation behind schur_cond_estimate for any CG run: the smallest and
+ * largest eigenvalue of the m x m Lanczos tridiagonal built from the step lengths
+ * alpha[0..m) (> 0) and direction coefficients beta[0..m-1) (>= 0).  No device work.
+ * SCHUR_EINVAL on null pointers, m < 1 or coefficients outside those ranges. */
+int schur_lanczos_extremes(const double* alpha, const double* beta, int m, double* lambda_min,
+                           double* lambda_max);
+
 /* Borrowed device pointer to a field (valid until the next solve/recover or destroy):
  * P (f64, cells), U (f64, faces), FLAGS (u8, faces), MASK (u8, cells), G (f64, cells). */
 int schur_get_field(schur_geom_t g, int which, void** dev_ptr, int64_t* elems, int* dtype);

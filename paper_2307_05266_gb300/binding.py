@@ -36,6 +36,7 @@ EXPORTED = [
     "schur_server_submit", "schur_server_progress", "schur_server_take", "schur_server_info",
     "schur_server_destroy",
     "schur_set_launch", "schur_permeability_diag", "schur_history", "schur_cond_estimate",
+    "schur_lanczos_extremes",
 ]
 KERNELS = {"cgA_dir": 0, "cgA_matvec": 1, "cgA_update": 2, "cgS_dir": 3, "cgS_matvec": 4,
            "cgS_update": 5, "cgA_dir_f32": 6, "cgA_matvec_f32": 7, "cgA_update_f32": 8,
@@ -117,6 +118,8 @@ def load(build_if_missing: bool = True):
         "schur_history": (C.c_int, [vp, C.c_int, vp, vp, vp, vp, C.POINTER(C.c_int)]),
         "schur_cond_estimate": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_double)]),
+        "schur_lanczos_extremes": (C.c_int, [vp, vp, C.c_int, C.POINTER(C.c_double),
+                                             C.POINTER(C.c_double)]),
         "schur_permeability_diag": (C.c_int, [vp, C.POINTER(Opts), C.POINTER(C.c_double),
                                               C.POINTER(Stats)]),
         "schur_permeability_noalloc": (C.c_int, [vp, vp, C.c_int, i64p, C.c_int64, vp, vp]),
@@ -474,6 +477,18 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def lanczos_extremes(alpha, beta):
+    """(lambda_min, lambda_max) of the Lanczos tridiagonal of a CG run (host computation of
+    the library, see schur_lanczos_extremes)."""
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    lo, hi = C.c_double(), C.c_double()
+    _check(load().schur_lanczos_extremes(a.ctypes.data_as(C.c_void_p),
+                                         b.ctypes.data_as(C.c_void_p) if b.size else None,
+                                         len(a), C.byref(lo), C.byref(hi)))
+    return lo.value, hi.value
 
 
 def footprint_bytes(shape, precision=FP64):

@@ -833,6 +833,24 @@ int schur_history(schur_geom_t G, int cap, double* alpha, double* beta, double* 
     return SCHUR_OK;
 }
 
+int schur_lanczos_extremes(const double* alpha, const double* beta, int m, double* lmin,
+                           double* lmax) {
+    if (!alpha || (m > 1 && !beta) || !lmin || !lmax || m < 1)
+        return set_error(SCHUR_EINVAL, "bad Lanczos arguments");
+    // Lanczos tridiagonal of CG (Saad, Section 6.7.3): T[j][j] = 1/a_j + b_(j-1)/a_(j-1),
+    // T[j][j+1] = sqrt(b_j)/a_j
+    std::vector<double> d(m), e(m > 1 ? m - 1 : 0);
+    for (int j = 0; j < m; ++j) {
+        if (!(alpha[j] > 0.0) || (j + 1 < m && !(beta[j] >= 0.0)))
+            return set_error(SCHUR_EINVAL, "CG coefficients must be alpha > 0, beta >= 0");
+        d[j] = 1.0 / alpha[j] + (j ? beta[j - 1] / alpha[j - 1] : 0.0);
+        if (j + 1 < m) e[j] = std::sqrt(beta[j]) / alpha[j];
+    }
+    *lmin = tridiag_eig(d, e, 0);
+    *lmax = tridiag_eig(d, e, m - 1);
+    return SCHUR_OK;
+}
+
 int schur_cond_estimate(schur_geom_t G, double* lmin, double* lmax, double* cond) {
     if (!G || !lmin || !lmax || !cond) return set_error(SCHUR_EINVAL, "null argument");
     Handle& H = G->H;
@@ -846,17 +864,8 @@ int schur_cond_estimate(schur_geom_t G, double* lmin, double* lmax, double* cond
     int n = 0;
     int rc = schur_history(G, m, a.data(), b.data(), nullptr, nullptr, &n);
     if (rc) return rc;
-    // Lanczos tridiagonal of CG (Saad, Section 6.7.3): T[j][j] = 1/a_j + b_(j-1)/a_(j-1),
-    // T[j][j+1] = sqrt(b_j)/a_j
-    std::vector<double> d(m), e(m > 1 ? m - 1 : 0);
-    for (int j = 0; j < m; ++j) {
-        if (!(a[j] > 0.0) || (j + 1 < m && !(b[j] >= 0.0)))
-            return set_error(SCHUR_ESTATE, "the recorded CG coefficients are not usable");
-        d[j] = 1.0 / a[j] + (j ? b[j - 1] / a[j - 1] : 0.0);
-        if (j + 1 < m) e[j] = std::sqrt(b[j]) / a[j];
-    }
-    *lmin = tridiag_eig(d, e, 0);
-    *lmax = tridiag_eig(d, e, m - 1);
+    rc = schur_lanczos_extremes(a.data(), b.data(), m, lmin, lmax);
+    if (rc) return set_error(SCHUR_ESTATE, "the recorded CG coefficients are not usable");
     *cond = *lmax / *lmin;
     return SCHUR_OK;
 }

@@ -98,3 +98,29 @@ def test_server_rejects_job_larger_than_budget_without_gpu(lib):
         srv.submit(np.ones((64, 64, 64), np.uint8))
     assert e.value.code == binding.SCHUR_ENOMEM
     srv.close()
+
+
+def test_lanczos_extremes_host_computation_matches_numpy(lib):
+    """The library's Sturm-bisection eigen-solve of the CG Lanczos tridiagonal (host code,
+    no GPU) against the oracle's dense eigvalsh on the same coefficients, from CG runs on
+    SPD matrices and from Algorithm 1 on a small Stokes problem."""
+    from oracle import krylov, stokes
+    from paper_2307_05266_gb300 import synth
+    rng = np.random.default_rng(3)
+    for n, span in ((12, 1e2), (40, 1e5)):
+        Q = np.linalg.qr(rng.standard_normal((n, n)))[0]
+        A = (Q * np.geomspace(1.0, span, n)) @ Q.T
+        res = krylov.pcg(lambda x: A @ x, rng.standard_normal(n), 1.0 / np.diag(A), 1e-14, 300)
+        m = min(len(res.alphas), len(res.betas) + 1)
+        lo, hi = binding.lanczos_extremes(res.alphas[:m], res.betas[:m - 1])
+        ref = krylov.lanczos_cond(res.alphas, res.betas)
+        assert lo == pytest.approx(ref[0], rel=1e-9) and hi == pytest.approx(ref[1], rel=1e-9)
+    m_ = synth.square_array_2d(2, 10, 4, 2, seed=1)
+    r = stokes.solve(m_, (1.0, 0.0), stokes.Options(precond=stokes.SIMPLE, tol=1e-10))
+    a, b = r["schur"].alphas, r["schur"].betas
+    lo, hi = binding.lanczos_extremes(a, b[:len(a) - 1])
+    ref = krylov.lanczos_cond(a, b)
+    assert hi / lo == pytest.approx(ref[2], rel=1e-9)
+    assert binding.lanczos_extremes([2.0], [])[0] == pytest.approx(0.5)   # 1 x 1: 1/alpha
+    with pytest.raises(binding.SchurError):
+        binding.lanczos_extremes([1.0, -1.0], [0.5])
