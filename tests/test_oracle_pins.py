@@ -432,3 +432,57 @@ def test_lanczos_cond_of_outer_cg_matches_dense(n_avg):
     est = krylov.lanczos_cond(r["schur"].alphas, r["schur"].betas)
     ref = dense.effective_cond(dense.preconditioned_spectrum(prob))
     assert 0.95 * ref <= est[2] <= ref * (1 + 1e-9)
+
+
+# ---- stopping rules (Section 3.2, Algorithm 1, Section 4.2.2) ----------------------
+def test_inner_stop_is_the_preconditioned_residual():
+    """Jacobi PCG stops at the first k with ||M^-1 r_k|| / ||M^-1 r_0|| < eps, r_k the
+    recursive residual: recomputed from the returned x (true residual), the ratio agrees
+    to rounding, and the unpreconditioned ratio is a different number."""
+    m = synth.sphere_packing(14, 2.0, 3.0, 0.5, seed=5)
+    prob = stokes.StokesProblem(m)
+    b = mac.force(prob.geo, (1.0, 0.0, 0.0))
+    minv = 1.0 / prob.dA
+    tol = 1e-6
+    res = prob.solve_A(b, tol, 20000)
+    z0 = np.linalg.norm(minv * b)
+    r = b - prob.A @ res.x
+    rel_pre = np.linalg.norm(minv * r) / z0
+    assert res.status == krylov.OK and rel_pre < tol * 1.01
+    assert res.rel == pytest.approx(rel_pre, rel=1e-4)
+    prev = prob.solve_A(b, tol, res.iters - 1)            # one iteration earlier: not yet
+    assert np.linalg.norm(minv * (b - prob.A @ prev.x)) / z0 >= tol * 0.99
+    rel_unpre = np.linalg.norm(r) / np.linalg.norm(b)
+    assert abs(rel_unpre - rel_pre) > 1e-3 * rel_pre
+
+
+@pytest.mark.parametrize("precond", [stokes.UZAWA, stokes.SIMPLE])
+def test_outer_preconditioned_stop_rule(precond):
+    """Algorithm 1's rule ||z_k|| / ||z_0|| < eps with z = S-hat^-1 r: recomputed from the
+    final pressure (r = g - S p, z = S-hat^+ r) it holds at the stop and not one
+    iteration earlier; for Uzawa z = r, so both norms coincide."""
+    m = synth.square_array_2d(2, 10, 4, 2, seed=1)
+    prob = stokes.StokesProblem(m)
+    f = (1.0, 0.0)
+    tol = 1e-5
+    opts = stokes.Options(precond=precond, stop_norm=krylov.STOP_PRECOND, tol=tol)
+    out, g = prob.solve(f, opts)
+    assert out.status == krylov.OK and out.outer_iters > 1
+    assert out.rel_res_precond < tol
+
+    def zrel(p):
+        r = g - prob.apply_S(p, 1e-13, 20000)[0]
+        if precond == stokes.UZAWA:
+            return np.linalg.norm(r) / np.linalg.norm(g)
+        r0 = prob.remove_mean(g.copy())
+        z0 = prob.solve_simple(r0, 1e-13, 20000).x
+        z = prob.solve_simple(prob.remove_mean(r), 1e-13, 20000).x
+        return np.linalg.norm(z) / np.linalg.norm(z0)
+
+    assert zrel(out.p) == pytest.approx(out.rel_res_precond, rel=1e-3)
+    early = stokes.Options(precond=precond, stop_norm=krylov.STOP_PRECOND, tol=tol,
+                           max_outer=out.outer_iters - 1)
+    out_e, _ = prob.solve(f, early)
+    assert out_e.status == krylov.NOT_CONVERGED and zrel(out_e.p) >= tol * 0.99
+    if precond == stokes.UZAWA:
+        assert out.rel_res_precond == pytest.approx(out.rel_res, rel=1e-12)
