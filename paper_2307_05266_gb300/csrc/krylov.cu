@@ -12,7 +12,9 @@
 // sums the dot products of all blocks in the same fixed order, so that all blocks hold
 // the same scalars and take the same decisions.  Each barrier wait is bounded; a wait
 // that runs out sets a sticky error flag, and every kernel, loop and the host call then
-// stop with an error status.  The phases also exist as single kernels for profiling.
+// stop with an error status.  The phases also run as single kernels, one graph node each
+// inside a conditional while node, in the per-phase launch shape (geometries that share
+// the GPU interleave better that way) and in the profiling hook.
 // The inner kernels are templates on the storage/arithmetic type T: FP64 for the plain
 // path, FP32 for the mixed-precision path (GB300 runs FP32 at 64x its FP64 rate).  Dot
 // products are summed per thread in T and across threads and blocks in FP64.
