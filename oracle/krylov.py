@@ -43,16 +43,19 @@ class CGResult:
 
 def pcg(apply, b: np.ndarray, minv: np.ndarray, tol: float, max_iter: int,
         project=None) -> CGResult:
-    """Jacobi-preconditioned CG from x_0 = 0.
+    """Preconditioned CG from x_0 = 0 (Jacobi in the paper's setting).
 
-    ``apply(v)`` returns the operator times v, ``minv`` is the inverse diagonal.
+    ``apply(v)`` returns the operator times v; ``minv`` is the inverse diagonal (Jacobi)
+    or a callable returning M^-1 r for a symmetric positive definite M (the multigrid of
+    ``oracle.amg``).
     ``project`` (optional) is applied to the returned solution; the SIMPLE solve uses
     it to remove the constant pressure mode (Section 3.2: the Neumann pressure
     Laplacian has the constant in its nullspace).
     """
+    prec = minv if callable(minv) else (lambda v: minv * v)
     x = np.zeros_like(b)
     r = b.copy()
-    z = minv * r
+    z = prec(r)
     z0 = float(np.sqrt(z @ z))
     if z0 == 0.0:
         return CGResult(x, 0, OK, 0.0)
@@ -69,7 +72,7 @@ def pcg(apply, b: np.ndarray, minv: np.ndarray, tol: float, max_iter: int,
         alpha = rho / dq
         x += alpha * d
         r -= alpha * q
-        z = minv * r
+        z = prec(r)
         rel = float(np.sqrt(z @ z)) / z0
         res.alphas.append(alpha)
         res.iters, res.rel = k, rel

@@ -12,7 +12,9 @@ Steps (Section 1, eqs. schur_system, schur_rhs, velocity_schur; Section 2.3):
    darcy_law with mu = 1, L = 1 and a unit force along the axis).
 
 Defaults follow the readings of the paper that the tests use: Jacobi inner
-preconditioners, zero initial guesses, eps_A = eps_S-hat = 1e-12.
+preconditioners, zero initial guesses, eps_A = eps_S-hat = 1e-12.  ``inner_precond =
+INNER_AMG`` replaces Jacobi in both inner solves by the aggregation multigrid of
+``oracle.amg`` (the paper uses BoomerAMG there, Section 3.2).
 """
 
 from __future__ import annotations
@@ -21,9 +23,10 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import krylov, mac
+from . import amg, krylov, mac
 
 UZAWA, SIMPLE = 0, 1
+INNER_JACOBI, INNER_AMG = 0, 1
 ZERO_RHS_RTOL = 1e-12
 
 
@@ -36,6 +39,7 @@ class Options:
     tol_inner_S: float = 1e-12
     max_outer: int = 2000
     max_inner: int = 20000
+    inner_precond: int = INNER_JACOBI
 
 
 class StokesProblem:
@@ -52,9 +56,23 @@ class StokesProblem:
         self.dS = self.S_simple.diagonal()
         self.n_comp, self.comp = fluid_components(self.geo)
         self.comp_size = np.bincount(self.comp, minlength=self.n_comp).astype(np.float64)
+        self._amg = {}                          # multigrid hierarchies, built on first use
+
+    def amg_levels(self, which: str):
+        """Aggregation-multigrid hierarchy of A ("A") or S-hat_simple ("S")."""
+        if which not in self._amg:
+            if which == "A":
+                self._amg[which] = amg.build(self.A, amg.face_coords(self.geo))
+            else:
+                self._amg[which] = amg.build(self.S_simple, amg.cell_coords(self.geo))
+        return self._amg[which]
 
     # ---- single operators -------------------------------------------------------
-    def solve_A(self, v, tol, max_iter):
+    def solve_A(self, v, tol, max_iter, inner=INNER_JACOBI):
+        if inner == INNER_AMG:
+            levels = self.amg_levels("A")
+            return krylov.pcg(lambda x: self.A @ x, v, lambda r: amg.vcycle(levels, r), tol,
+                              max_iter)
         return krylov.pcg(lambda x: self.A @ x, v, 1.0 / self.dA, tol, max_iter)
 
     def remove_mean(self, p):
@@ -66,18 +84,23 @@ class StokesProblem:
         mean = np.bincount(self.comp, weights=p, minlength=self.n_comp) / self.comp_size
         return p - mean[self.comp]
 
-    def solve_simple(self, r, tol, max_iter):
+    def solve_simple(self, r, tol, max_iter, inner=INNER_JACOBI):
         """z = S-hat_simple^+ r.  The "special care" of Section 3.2 for the singular
         pressure operator, read as: the right-hand side is projected onto the range first
         (rounding leaves it a component along the constants that grows relative to r as
         the outer residual shrinks, and CG on an inconsistent system does not converge),
         and the returned solution is projected as well."""
-        minv = np.where(self.dS > 0, 1.0 / np.where(self.dS > 0, self.dS, 1.0), 0.0)
+        if inner == INNER_AMG:
+            # the cycle's output is projected too, so that CG stays in the range
+            levels = self.amg_levels("S")
+            minv = lambda v: self.remove_mean(amg.vcycle(levels, v))  # noqa: E731
+        else:
+            minv = np.where(self.dS > 0, 1.0 / np.where(self.dS > 0, self.dS, 1.0), 0.0)
         return krylov.pcg(lambda x: self.S_simple @ x, self.remove_mean(r), minv, tol,
                           max_iter, project=self.remove_mean)
 
-    def apply_S(self, d, tol_A, max_inner):
-        res = self.solve_A(self.BT @ d, tol_A, max_inner)
+    def apply_S(self, d, tol_A, max_inner, inner=INNER_JACOBI):
+        res = self.solve_A(self.BT @ d, tol_A, max_inner, inner)
         return self.B @ res.x, res.iters
 
     # ---- the path ---------------------------------------------------------------
@@ -88,7 +111,8 @@ class StokesProblem:
         a flow that is exactly divergence-free (e.g. the x-invariant channel flow) is
         rounding noise, and Algorithm 1 started on noise has nothing to converge to.
         """
-        res = self.solve_A(mac.force(self.geo, f), opts.tol_inner_A, opts.max_inner)
+        res = self.solve_A(mac.force(self.geo, f), opts.tol_inner_A, opts.max_inner,
+                           opts.inner_precond)
         g = self.B @ res.x
         scale = float(np.linalg.norm(abs(self.B) @ np.abs(res.x)))
         zero = float(np.linalg.norm(g)) <= ZERO_RHS_RTOL * scale
@@ -103,7 +127,7 @@ class StokesProblem:
             return out, g
 
         def apply_S(d):
-            return self.apply_S(d, opts.tol_inner_A, opts.max_inner)
+            return self.apply_S(d, opts.tol_inner_A, opts.max_inner, opts.inner_precond)
 
         if opts.precond == UZAWA:
             def precond(r):
@@ -111,7 +135,8 @@ class StokesProblem:
         else:
             def precond(r):
                 r[:] = self.remove_mean(r)      # the outer residual is projected in place
-                res = self.solve_simple(r, opts.tol_inner_S, opts.max_inner)
+                res = self.solve_simple(r, opts.tol_inner_S, opts.max_inner,
+                                        opts.inner_precond)
                 return res.x, res.iters
 
         out = krylov.schur_pcg(apply_S, g, precond, opts.tol, opts.max_outer,
@@ -122,7 +147,7 @@ class StokesProblem:
     def recover_velocity(self, f, p, opts: Options = None):
         opts = opts or Options()
         rhs = mac.force(self.geo, f) - self.BT @ p
-        return self.solve_A(rhs, opts.tol_inner_A, opts.max_inner)
+        return self.solve_A(rhs, opts.tol_inner_A, opts.max_inner, opts.inner_precond)
 
     def permeability(self, u, axis: int) -> float:
         g = self.geo
