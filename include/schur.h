@@ -261,8 +261,9 @@ int schur_set_launch(schur_geom_t g, int blocks_per_sm, int entries_per_thread,
  * It calls no cudaMalloc or cudaFree: its scratch is a static device array of 96 KiB
  * held by every device that loads the library until exit, so ndim * face_stride may not
  * exceed 8388608 faces (SCHUR_EINVAL otherwise).  The first call on a device looks up
- * the array's device address; make that first call before any stream capture.  All
- * calls share the array: calls that overlap on the GPU race and must be serialised. */
+ * the array's device address (and so does the first call after a device reset, which
+ * replaces the context); make that first call before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU race and must be serialised. */
 int schur_permeability_noalloc(const double* u, const uint8_t* flags, int ndim,
                                const int64_t dims[3], int64_t face_stride, void* stream,
                                double* k_dev);

@@ -1208,9 +1208,10 @@ __global__ void k_fcg_dots(Dev g, Compact C, const int* __restrict__ cmpc,
         const double zc = simple ? (double)sx[m] - cmean[cmpc[m]] : rv[c];
         v[0] += zc * qv[c];
     }
-    if (reduce_last_block<1>(v, partials, &ctl->ticket) && is_thread0())
+    if (reduce_last_block<1>(v, partials, &ctl->ticket) && is_thread0()) {
         o->beta = -v[0] / ctl->mix.dq;
         hist_put(ctl, o->iter - 1, H_BETA, o->beta);
+    }
 }
 
 // True residual r = g - B u with u = A^-1 B^T p from an FP64 inner solve; decides whether

@@ -31,7 +31,38 @@ static __device__ __align__(256) StaticScratch g_scratch;
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
+// Per device: the array's device address and the id of the context it was looked up in.
+// A device reset (cudaDeviceReset, which some host frameworks call) replaces the primary
+// context and reloads the module, so the address is looked up again when the current
+// context's id differs from the cached one.
 StaticScratch* g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
+
+// Driver entry points for the context id, resolved through the runtime (the library does
+// not link the driver library directly).
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
+
+cudaError_t current_context_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000,
+                                                         cudaEnableDefault, &q1);
+        if (e != cudaSuccess) return e;
+        e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess) return e;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return cudaErrorNotSupported;
+        get_current = (CtxGetCurrentFn)f1;
+        get_id = (CtxGetIdFn)f2;
+    }
+    void* ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx) return cudaErrorDeviceUninitialized;
+    return get_id(ctx, id) == 0 ? cudaSuccess : cudaErrorUnknown;
+}
 
 __global__ void k_perm_static(const double* __restrict__ u, const uint8_t* __restrict__ flags,
                               long long stride, int d, long long ncell,
@@ -79,15 +110,27 @@ extern "C" int schur_permeability_noalloc(const double* u, const uint8_t* flags,
         return schur_set_error_internal(SCHUR_EINVAL, "device ordinal beyond 63");
     StaticScratch* sc = nullptr;
     {
-        // set-up, once per device, with that device current: the host-side name of the
-        // static array is not a device address, so ask the runtime for the real one
+        // set-up, once per device (and again after a device reset), with that device
+        // current: the host-side name of the static array is not a device address, so ask
+        // the runtime for the real one
         std::lock_guard<std::mutex> lock(g_mutex);
-        if (!g_scratch_ptr[dev]) {
+        unsigned long long ctx = 0;
+        e = current_context_id(&ctx);
+        if (e == cudaErrorDeviceUninitialized) {
+            // no context on this thread yet: the symbol lookup below creates the primary
+            // context, after which its id can be read
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_scratch);
+            if (e == cudaSuccess) e = current_context_id(&ctx);
+        }
+        if (e != cudaSuccess) return schur_set_error_internal(SCHUR_ECUDA, cudaGetErrorString(e));
+        if (!g_scratch_ptr[dev] || g_scratch_ctx[dev] != ctx) {
             void* p = nullptr;
             e = cudaGetSymbolAddress(&p, g_scratch);
             if (e != cudaSuccess)
                 return schur_set_error_internal(SCHUR_ECUDA, cudaGetErrorString(e));
             g_scratch_ptr[dev] = (StaticScratch*)p;
+            g_scratch_ctx[dev] = ctx;
         }
         sc = g_scratch_ptr[dev];
     }
