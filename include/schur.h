@@ -250,6 +250,19 @@ int schur_time_kernel(schur_geom_t g, int kernel, float* ms);
 int schur_set_launch(schur_geom_t g, int blocks_per_sm, int entries_per_thread,
                      int persistent_inner);
 
+/* Bound of the grid-barrier waits inside the persistent inner-solve kernels of this
+ * geometry (no counterpart in the paper: the failure path of the cooperative launches).
+ * A wait polls the arrival counter at most `polls` times (0: the default, about ten
+ * seconds); when it runs out, the kernel sets a sticky flag, every block leaves its loop
+ * at its next barrier, the outer loops stop, and the call returns SCHUR_ECUDA with
+ * schur_last_error() naming the barrier.  skip_block >= 0 makes that block of every loop
+ * kernel leave out its barrier arrivals, so that the other blocks' waits run out: a test
+ * hook for the failure path (it faults nothing and every wait still ends); -1 turns it
+ * off.  Both settings stay on the handle until changed; the next solve starts with the
+ * flag cleared.  Errors: SCHUR_EINVAL (skip_block out of range), SCHUR_ESTATE (an
+ * asynchronous solve is in flight). */
+int schur_set_barrier_limit(schur_geom_t g, unsigned int polls, int skip_block);
+
 /* Allocation-free Darcy permeability of a caller-owned velocity field (no counterpart in
  * the paper: an entry point for callers that may not allocate device memory, e.g. code
  * running inside a memory pool it does not own or inside an already-captured graph).

@@ -36,7 +36,7 @@ EXPORTED = [
     "schur_server_submit", "schur_server_progress", "schur_server_take", "schur_server_info",
     "schur_server_destroy",
     "schur_set_launch", "schur_permeability_diag", "schur_history", "schur_cond_estimate",
-    "schur_lanczos_extremes",
+    "schur_lanczos_extremes", "schur_set_barrier_limit",
 ]
 KERNELS = {"cgA_dir": 0, "cgA_matvec": 1, "cgA_update": 2, "cgS_dir": 3, "cgS_matvec": 4,
            "cgS_update": 5, "cgA_dir_f32": 6, "cgA_matvec_f32": 7, "cgA_update_f32": 8,
@@ -115,6 +115,7 @@ def load(build_if_missing: bool = True):
         "schur_solve_A": (C.c_int, [vp, vp, vp, C.c_double, C.c_int, C.POINTER(C.c_int)]),
         "schur_time_kernel": (C.c_int, [vp, C.c_int, C.POINTER(C.c_float)]),
         "schur_set_launch": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
+        "schur_set_barrier_limit": (C.c_int, [vp, C.c_uint, C.c_int]),
         "schur_history": (C.c_int, [vp, C.c_int, vp, vp, vp, vp, C.POINTER(C.c_int)]),
         "schur_cond_estimate": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_double)]),
@@ -295,6 +296,11 @@ class Geometry:
 
     def apply_simple(self, p, q):
         _check(load().schur_apply_simple(self._h, _ptr(p), _ptr(q)))
+
+    def set_barrier_limit(self, polls=0, skip_block=-1):
+        """Poll limit of the loop kernels' grid-barrier waits (0: default) and the block
+        that leaves out its arrivals for testing the bounded wait (-1: none)."""
+        _check(load().schur_set_barrier_limit(self._h, polls, skip_block))
 
     def solve_async(self, **kw):
         _check(load().schur_solve_async(self._h, C.byref(default_opts(**kw))))

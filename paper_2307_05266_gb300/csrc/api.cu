@@ -972,6 +972,17 @@ int schur_set_launch(schur_geom_t G, int blocks_per_sm, int entries_per_thread,
     return set_launch_shape(G->H, blocks_per_sm, entries_per_thread, persistent_inner);
 }
 
+int schur_set_barrier_limit(schur_geom_t G, unsigned int polls, int skip_block) {
+    if (!G) return set_error(SCHUR_EINVAL, "null handle");
+    if (skip_block < -1 || skip_block >= kMaxBlocks)
+        return set_error(SCHUR_EINVAL, "skip_block must be -1 or a block index below 4096");
+    Handle& H = G->H;
+    if (H.pending) return set_error(SCHUR_ESTATE, "an asynchronous solve is in flight");
+    H.hctl->bar_limit = polls;
+    H.hctl->bar_skip = skip_block + 1;
+    return SCHUR_OK;
+}
+
 int schur_time_kernel(schur_geom_t G, int kernel, float* ms) {
     if (!G || !ms) return set_error(SCHUR_EINVAL, "null argument");
     if (kernel < 0 || kernel > 15) return set_error(SCHUR_EINVAL, "kernel id must be 0..15");

@@ -118,6 +118,11 @@ struct Ctl {
     // when a wait ran past its limit
     unsigned int bar_count;
     unsigned int bar_err;
+    // poll limit of one barrier wait (0: kBarrierSpins), and, for testing the bounded
+    // wait, 1 + the index of a block that leaves out its barrier arrivals (0: none); both
+    // are set per handle by schur_set_barrier_limit and kept across calls
+    unsigned int bar_limit;
+    int bar_skip;
     // per-iteration record of the outer iteration (4 doubles per iteration: alpha, beta,
     // ||r||/||r_0||, ||z||/||z_0||; NaN where a value was not formed); null: no record
     double* hist;
@@ -262,13 +267,14 @@ __device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned& target) {
     __syncthreads();
     target += gridDim.x;
     if (threadIdx.x == 0) {
+        const unsigned limit = ctl->bar_limit ? ctl->bar_limit : kBarrierSpins;
         __threadfence();
-        atomicAdd(&ctl->bar_count, 1u);
+        if ((int)blockIdx.x + 1 != ctl->bar_skip) atomicAdd(&ctl->bar_count, 1u);
         unsigned ok = 1u;
         for (unsigned spin = 0;; ++spin) {
             if ((int)(ld_acquire_u32(&ctl->bar_count) - target) >= 0) break;
             if (ld_acquire_u32(&ctl->bar_err) != 0u) { ok = 0u; break; }
-            if (spin >= kBarrierSpins) {
+            if (spin >= limit) {
                 atomicExch(&ctl->bar_err, 1u);
                 ok = 0u;
                 break;

@@ -14,7 +14,8 @@ import torch
 from oracle import mac, stokes
 from paper_2307_05266_gb300 import binding, synth
 
-from gpu_helpers import cell_device_to_compact, face_device_to_compact
+from gpu_helpers import (cell_device_to_compact, check_pressure, check_velocity,
+                         face_device_to_compact)
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -99,3 +100,47 @@ def test_tight256_properties_at_full_size():
         g.solve(precond=binding.SIMPLE, precision=binding.MIXED, tol=1e-8)
         g.recover_velocity()
         assert abs(g.permeability(0) - k64) <= 1e-6 * abs(k64)
+
+
+# 48^3 periodic packing, radii U[3, 6), porosity 0.40, seed 7: 115,112 unknown faces and
+# 44,169 fluid cells in one component of 44,115 cells plus 45 small ones, so the persistent
+# loops take several grid-stride steps per thread and both per-component reductions (the
+# grid-wide one for big components, the warp-per-component one for small ones) run.
+FIELD_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def field48():
+    mask = synth.sphere_packing(48, 3.0, 6.0, 0.40, 7)
+    f = (1.0, 0.0, 0.0)
+    refs = {pc: stokes.solve(mask, f, stokes.Options(precond=pc, tol=FIELD_TOL))
+            for pc in (stokes.UZAWA, stokes.SIMPLE)}
+    from oracle import krylov
+    lam_min, _, _ = krylov.lanczos_cond(refs[stokes.UZAWA]["schur"].alphas,
+                                        refs[stokes.UZAWA]["schur"].betas)
+    return mask, f, refs, lam_min
+
+
+@pytest.mark.parametrize("pc", [binding.UZAWA, binding.SIMPLE])
+def test_field_parity_48(field48, pc):
+    """u, p (modulo per-component constants) and k of the FP64 CUDA path against the
+    oracle on the same 48^3 mask, element by element."""
+    mask, f, refs, lam_min = field48
+    ref = refs[pc]
+    prob = ref["problem"]
+    geo = prob.geo
+    assert prob.n_comp > 1 and np.bincount(prob.comp).max() >= 2048
+    torch.cuda.set_device(0)
+    with binding.Geometry(mask) as g:
+        g.set_force(f)
+        st = g.solve(precond=pc, tol=FIELD_TOL)
+        rec = g.recover_velocity()
+        assert st.status == binding.SCHUR_OK
+        assert abs(st.outer_iters - ref["schur"].outer_iters) <= 2
+        assert abs(rec.inner_iters_A - ref["recovery"].iters) <= 2
+        u = face_device_to_compact(g, geo, g.field(binding.FIELD_U))
+        p = cell_device_to_compact(geo, g.field(binding.FIELD_P))
+        check_velocity(prob, geo, f, u, ref["u"])
+        check_pressure(geo, p, ref["p"], ref["g"], FIELD_TOL, lam_min)
+        for a in range(3):
+            assert abs(g.permeability(a) - ref["k"][a]) <= 1e-8 * abs(ref["k"][0])

@@ -13,9 +13,9 @@ import torch
 from oracle import krylov, mac, stokes
 from paper_2307_05266_gb300 import binding, synth
 
-from gpu_helpers import (cell_compact_to_device, cell_device_to_compact,
-                         face_compact_to_device,
-                         face_device_to_compact)
+from gpu_helpers import (cell_compact_to_device, cell_device_to_compact, check_pressure,
+                         check_velocity, face_compact_to_device, face_device_to_compact,
+                         smallest_schur_eigenvalue)
 
 pytestmark = pytest.mark.gpu
 
@@ -151,16 +151,12 @@ def test_full_solve_matches_oracle(cuda, name, force, tol, iters_comparable, pre
     g.recover_velocity()
     p = cell_device_to_compact(geo, g.field(binding.FIELD_P))
     u = face_device_to_compact(g, geo, g.field(binding.FIELD_U))
-    # velocity: relative L2 within 1e-9 of the flow scale max(||u||, ||A^-1 f||); the
-    # second term matters where the force is balanced by pressure and u is ~0
-    u_f = prob.solve_A(mac.force(geo, force), 1e-12, 20000).x
-    scale_u = max(np.linalg.norm(ref["u"]), np.linalg.norm(u_f))
-    assert np.linalg.norm(u - ref["u"]) <= 1e-9 * scale_u
-    # pressure (defined up to constants per component): both iterates meet
-    # ||S p - g|| <= tol ||g||, so ||S (p - p_ref)|| <= 2 tol ||g|| plus the inner-solve slack
+    check_velocity(prob, geo, force, u, ref["u"])
     if np.linalg.norm(ref["g"]) > 0 and st.outer_iters > 0:
         sdp, _ = prob.apply_S(p - ref["p"], 1e-13, 20000)
         assert np.linalg.norm(sdp) <= 3 * tol * np.linalg.norm(ref["g"])
+        lam_min = smallest_schur_eigenvalue(mask, per, force, tol)
+        check_pressure(geo, p, ref["p"], ref["g"], tol, lam_min)
     for a in range(geo.d):
         k = g.permeability(a)
         assert abs(k - ref["k"][a]) <= 1e-8 * abs(ref["k"][a]) + 1e-9 * geo.h ** 2
@@ -366,3 +362,30 @@ def test_invariants_and_host_side_faults(cuda):
         k, _ = g.permeability_diag(precond=binding.SIMPLE, tol=1e-10)
         assert k[1] > 0 and k[2] > 0
         assert abs(k[0]) <= 1e-9 * k[1]
+
+
+@pytest.mark.parametrize("precision", [binding.FP64, binding.MIXED])
+def test_bounded_barrier_wait_runs_out(cuda, precision):
+    """Every grid-barrier wait of the persistent inner-solve kernels is bounded: with one
+    block leaving out its arrivals and a limit of 2^10 polls, the other blocks' waits run
+    out, the kernels leave their loops, and the call reports SCHUR_ECUDA naming the
+    barrier instead of hanging.  Afterwards the same handle (hook off) and a fresh one
+    solve normally and agree bitwise."""
+    mask = synth.sphere_packing(20, 2.0, 4.0, 0.45, seed=2)
+    opts = dict(precond=binding.SIMPLE, precision=precision, tol=1e-8)
+    with binding.Geometry(mask) as g:
+        g.set_barrier_limit(1 << 10, skip_block=0)
+        with pytest.raises(binding.SchurError) as e:
+            g.solve(**opts)
+        assert e.value.code == binding.SCHUR_ECUDA
+        assert "ran past its limit" in str(e.value)
+        g.set_barrier_limit(0, -1)
+        st = g.solve(**opts)
+        g.recover_velocity()
+        k_same = g.permeability(0)
+        with pytest.raises(binding.SchurError):
+            g.set_barrier_limit(0, 4096)
+    with binding.Geometry(mask) as g:
+        st2 = g.solve(**opts)
+        g.recover_velocity()
+        assert st2.outer_iters == st.outer_iters and g.permeability(0) == k_same

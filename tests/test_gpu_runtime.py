@@ -12,9 +12,33 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import stokes
 from paper_2307_05266_gb300 import binding, synth
 
 pytestmark = pytest.mark.gpu
+
+# members of the batch and jobs of the server that are also checked against the oracle
+ORACLE_MEMBERS = (0, 2, 5)
+_ORACLE_K = {}
+
+
+def _oracle_k(i, mask, axis, precond, tol=1e-8):
+    """The FP64 oracle's permeability of mask i along `axis` (cached per test module)."""
+    key = (i, axis, precond, tol)
+    if key not in _ORACLE_K:
+        f = [0.0, 0.0, 0.0]
+        f[axis] = 1.0
+        ref = stokes.solve(mask, tuple(f), stokes.Options(precond=precond, tol=tol))
+        _ORACLE_K[key] = ref["k"][axis]
+    return _ORACLE_K[key]
+
+
+def _check_oracle_k(i, mask, axis, precond, k, precision):
+    """Batched and served results against the oracle: k within 1e-8 (FP64) or 1e-6
+    (mixed precision) of the oracle's k on the same mask and axis."""
+    k_ref = _oracle_k(i, mask, axis, precond)
+    rtol = 1e-8 if precision == binding.FP64 else 1e-6
+    assert abs(k - k_ref) <= rtol * abs(k_ref), (i, k, k_ref)
 
 
 def _masks():
@@ -64,6 +88,8 @@ def test_batch_equals_individual(precision):
         for i, ref in enumerate(refs):
             assert ss[i].outer_iters == ref[0]
             assert ks[i][0] == ref[2]
+    for i in ORACLE_MEMBERS:
+        _check_oracle_k(i, masks[i], 0, stokes.SIMPLE, ks[i][0], precision)
     b.close()
     for g in geoms:
         g.close()
@@ -82,6 +108,8 @@ def test_batch_autotune_keeps_results():
     ss, rs, ks = b.run()
     for i, ref in enumerate(refs):
         assert abs(ks[i][0] - ref[2]) <= 1e-6 * abs(ref[2])
+    for i in ORACLE_MEMBERS:
+        _check_oracle_k(i, masks[i], 0, stokes.UZAWA, ks[i][0], binding.MIXED)
     b.close()
     for g in geoms:
         g.close()
@@ -119,6 +147,8 @@ def test_server_results_alone_equal_in_mix():
     for mask, ax, r in zip(masks, axes, mixed):
         ref = _alone(mask, ax, **opts)
         assert abs(r["k"] - ref[2]) <= 1e-6 * abs(ref[2])
+    for i in ORACLE_MEMBERS:
+        _check_oracle_k(i, masks[i], axes[i], stokes.SIMPLE, mixed[i]["k"], binding.MIXED)
 
 
 def test_server_admission_respects_budget():
