@@ -71,8 +71,8 @@ class StokesProblem:
     def solve_A(self, v, tol, max_iter, inner=INNER_JACOBI):
         if inner == INNER_AMG:
             levels = self.amg_levels("A")
-            return krylov.pcg(lambda x: self.A @ x, v, lambda r: amg.vcycle(levels, r), tol,
-                              max_iter)
+            return krylov.pcg(lambda x: self.A @ x, v,
+                              lambda r: amg.vcycle(levels, r, amg.GAMMA_A), tol, max_iter)
         return krylov.pcg(lambda x: self.A @ x, v, 1.0 / self.dA, tol, max_iter)
 
     def remove_mean(self, p):
@@ -91,9 +91,12 @@ class StokesProblem:
         the outer residual shrinks, and CG on an inconsistent system does not converge),
         and the returned solution is projected as well."""
         if inner == INNER_AMG:
-            # the cycle's output is projected too, so that CG stays in the range
+            # The cycle's output is not projected: r stays in the range of S-hat (r = b -
+            # S-hat x with b in the range), so a nullspace part of z = M^-1 r changes
+            # neither r.z nor S-hat d; it enters only the stop norm ||z||, and the
+            # returned solution is projected.
             levels = self.amg_levels("S")
-            minv = lambda v: self.remove_mean(amg.vcycle(levels, v))  # noqa: E731
+            minv = lambda v: amg.vcycle(levels, v, amg.GAMMA_S)  # noqa: E731
         else:
             minv = np.where(self.dS > 0, 1.0 / np.where(self.dS > 0, self.dS, 1.0), 0.0)
         return krylov.pcg(lambda x: self.S_simple @ x, self.remove_mean(r), minv, tol,

@@ -548,17 +548,21 @@ def test_outer_preconditioned_stop_rule(precond):
 
 # ---- aggregation multigrid inner preconditioner (oracle.amg) -------------------------
 def test_amg_vcycle_is_symmetric_positive_definite():
-    """The V-cycle with adjoint Jacobi pre/post-smoothing is a symmetric positive definite
-    operator on A's space (the property CG needs of a preconditioner)."""
+    """The V-cycle with adjoint Jacobi pre/post-smoothing and the scaled coarse correction
+    is a symmetric positive definite operator, for A and for S-hat (the property CG needs
+    of a preconditioner)."""
     from oracle import amg
     m = synth.sphere_packing(8, 1.5, 2.5, 0.6, seed=2)
     prob = stokes.StokesProblem(m)
-    levels = amg.build(prob.A, amg.face_coords(prob.geo), min_coarse=16)
-    assert len(levels) >= 3
-    n = prob.A.shape[0]
-    M = np.column_stack([amg.vcycle(levels, e) for e in np.eye(n)])
-    assert np.abs(M - M.T).max() <= 1e-12 * np.abs(M).max()
-    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+    for op, coords, gamma, n_last in ((prob.A, amg.face_coords(prob.geo), amg.GAMMA_A, 3),
+                                      (prob.S_simple, amg.cell_coords(prob.geo), amg.GAMMA_S, 1)):
+        levels = amg.build(op, coords)
+        assert len(levels) == 4                      # 8^3 -> 4^3 -> 2^3 -> 1^3
+        assert levels[-1].A.shape[0] == n_last       # one unknown per component
+        n = op.shape[0]
+        M = np.column_stack([amg.vcycle(levels, e, gamma) for e in np.eye(n)])
+        assert np.abs(M - M.T).max() <= 1e-12 * np.abs(M).max()
+        assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
 
 
 def test_amg_coarse_operator_of_the_empty_box():
@@ -568,7 +572,7 @@ def test_amg_coarse_operator_of_the_empty_box():
     internal couplings = 24 on the diagonal, and 4 fine couplings cross each face)."""
     from oracle import amg
     prob = stokes.StokesProblem(np.ones((8, 8, 8), np.uint8))
-    levels = amg.build(prob.S_simple, amg.cell_coords(prob.geo), min_coarse=8)
+    levels = amg.build(prob.S_simple, amg.cell_coords(prob.geo))
     Ac = levels[1].A.toarray()
     n = 4
     lap1 = 2 * np.eye(n) - np.roll(np.eye(n), 1, axis=0) - np.roll(np.eye(n), -1, axis=0)
@@ -611,3 +615,26 @@ def test_full_solve_with_amg_inner_solves(precond):
     assert ra["schur"].status == krylov.OK
     assert abs(ra["k"][0] - rj["k"][0]) <= 1e-8 * abs(rj["k"][0])
     assert ra["schur"].inner_iters_A < rj["schur"].inner_iters_A
+
+
+def test_amg_isolated_pore_is_a_nullspace_unknown():
+    """A fluid voxel with solid on every side is a pore of its own: its S-hat row is zero
+    (diagonal mass 0) and its weight in smoothing and in the coarsest solve is 0; an
+    aggregate that is a whole pore of two voxels has coarse diagonal 0 (its couplings stay
+    inside the aggregate) and weight 0, although its diagonal mass is positive."""
+    from oracle import amg
+    m = np.ones((8, 8, 8), np.uint8)
+    m[0:6, 0:6, 0:6] = 0
+    m[1, 1, 1] = 1                              # isolated voxel
+    m[2, 2, 2] = m[2, 2, 3] = 1                 # two-voxel pore inside aggregate (1, 1, 1)
+    prob = stokes.StokesProblem(m)
+    levels = amg.build(prob.S_simple, amg.cell_coords(prob.geo))
+    c = prob.geo.pidx
+    assert levels[0].dinv[c[1, 1, 1]] == 0.0 and levels[0].dinv[c[2, 2, 2]] > 0
+    lone = levels[0].P[c[1, 1, 1]].indices[0]
+    pair = levels[0].P[c[2, 2, 2]].indices[0]
+    assert levels[0].P[c[2, 2, 3]].indices[0] == pair and pair != lone
+    assert abs(levels[1].A[pair, pair]) <= 1e-15 and levels[1].dinv[pair] == 0.0
+    assert levels[1].dinv[lone] == 0.0
+    z = amg.vcycle(levels, np.ones(prob.geo.n_p), amg.GAMMA_S)
+    assert z[c[1, 1, 1]] == 0.0
