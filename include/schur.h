@@ -61,6 +61,11 @@ enum { SCHUR_PRECOND_AUTO = 2 };
 enum { SCHUR_STOP_UNPRECOND = 0, SCHUR_STOP_PRECOND = 1 };
 enum { SCHUR_FP64 = 0, SCHUR_MIXED = 1 };
 enum { SCHUR_LOOP_GRAPH = 0, SCHUR_LOOP_HOST = 1 };
+/* Preconditioner of the inner A and S-hat solves: Jacobi (the diagonal), or an aggregation
+ * multigrid V-cycle (2 x 2 x 2 voxel aggregates, Galerkin coarse operators down to a single
+ * cell solved exactly, one weighted-Jacobi sweep before and after the coarse correction);
+ * the paper uses BoomerAMG there (Section 3.2). */
+enum { SCHUR_INNER_JACOBI = 0, SCHUR_INNER_MG = 1 };
 enum { SCHUR_FIELD_P = 0, SCHUR_FIELD_U = 1, SCHUR_FIELD_FLAGS = 2, SCHUR_FIELD_MASK = 3,
        SCHUR_FIELD_G = 4 };
 enum { SCHUR_DTYPE_U8 = 0, SCHUR_DTYPE_F32 = 1, SCHUR_DTYPE_F64 = 2 };
@@ -72,7 +77,7 @@ typedef struct schur_server* schur_server_t;
 /* Solver options.  Defaults (schur_opts_default): SIMPLE, unpreconditioned stop,
  * FP64, graph loop, tol 1e-8, tol_inner_A = tol_inner_S = 1e-12, max_outer 2000,
  * max_inner 20000; mixed precision: tol_inner_f32 1e-4, refine_factor 1e-3,
- * max_refine 30, step_max 1000. */
+ * max_refine 30, step_max 1000; Jacobi inner preconditioner. */
 typedef struct {
     int precond;        /* SCHUR_UZAWA | SCHUR_SIMPLE (eq. schur_uzawa_prec) | _PRECOND_AUTO  */
     int stop_norm;      /* SCHUR_STOP_UNPRECOND: ||r_k||/||r_0|| < tol (Section 4.2.2);
@@ -92,6 +97,9 @@ typedef struct {
     double refine_factor;  /* MIXED: residual reduction of one refinement step (1e-3)       */
     int max_refine;        /* MIXED: cap on refinement steps (true residuals) (30)          */
     int step_max;          /* MIXED: cap on FCG iterations in one step (1000)               */
+    int inner_precond;     /* SCHUR_INNER_JACOBI (default) | SCHUR_INNER_MG: preconditioner of
+                              every inner solve of the call (and of the recovery that follows);
+                              multigrid inner solves always run as persistent loop kernels   */
 } schur_opts;
 
 typedef struct {

@@ -17,8 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIBNAME = "libschur.so"
-SOURCES = ["geometry.cu", "krylov.cu", "api.cu", "noalloc.cu", "runtime.cu"]
-HEADERS = ["common.cuh", "internal.h"]
+SOURCES = ["geometry.cu", "krylov.cu", "mg.cu", "api.cu", "noalloc.cu", "runtime.cu"]
+HEADERS = ["common.cuh", "internal.h", "cg_dev.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -23,6 +23,7 @@ AUTO_SIMPLE_BELOW = 0.25
 STOP_UNPRECOND, STOP_PRECOND = 0, 1
 FP64, MIXED = 0, 1
 LOOP_GRAPH, LOOP_HOST = 0, 1
+INNER_JACOBI, INNER_MG = 0, 1
 FIELD_P, FIELD_U, FIELD_FLAGS, FIELD_MASK, FIELD_G = 0, 1, 2, 3, 4
 
 EXPORTED = [
@@ -51,7 +52,7 @@ class Opts(C.Structure):
                 ("loop_mode", C.c_int), ("max_outer", C.c_int), ("max_inner", C.c_int),
                 ("tol", C.c_double), ("tol_inner_A", C.c_double), ("tol_inner_S", C.c_double),
                 ("tol_inner_f32", C.c_double), ("refine_factor", C.c_double),
-                ("max_refine", C.c_int), ("step_max", C.c_int)]
+                ("max_refine", C.c_int), ("step_max", C.c_int), ("inner_precond", C.c_int)]
 
 
 class Stats(C.Structure):

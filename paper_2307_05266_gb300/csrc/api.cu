@@ -111,6 +111,8 @@ void free_all(Handle& H) {
                     H.nbA, H.nbS, H.codeS, H.dSc, H.hist};
     for (void* b : bufs)
         if (b) cudaFree(b);
+    mg_free(H.mgA);
+    mg_free(H.mgS);
     if (H.hctl) cudaFreeHost(H.hctl);
     if (H.ev0) cudaEventDestroy(H.ev0);
     if (H.ev1) cudaEventDestroy(H.ev1);
@@ -270,8 +272,9 @@ int build_components(Handle& H, const uint8_t* m) {
     A(&H.invdSc, np);
     A(&H.dSc, np);
     // p vectors carry one more entry, kept at 0, that missing stencil neighbours point at
-    A(&H.ax, nu); A(&H.ar, nu); A(&H.ap, nu + 1); A(&H.aq, nu);
-    A(&H.sx, np); A(&H.sr, np); A(&H.sp, np + 1); A(&H.sq, np);
+    // (r also: the multigrid smoother gathers r at stencil neighbours)
+    A(&H.ax, nu); A(&H.ar, nu + 1); A(&H.ap, nu + 1); A(&H.aq, nu);
+    A(&H.sx, np); A(&H.sr, np + 1); A(&H.sp, np + 1); A(&H.sq, np);
     H.ldA = (long long)(nu + 31) / 32 * 32;
     H.ldS = (long long)(np + 31) / 32 * 32;
     A(&H.nbA, (size_t)(2 * g.d * H.ldA));
@@ -399,6 +402,8 @@ int check_opts(const schur_opts& o) {
                                        "0 < refine_factor < 1, max_refine >= 1, step_max >= 1");
     if (o.loop_mode != SCHUR_LOOP_GRAPH && o.loop_mode != SCHUR_LOOP_HOST)
         return set_error(SCHUR_EINVAL, "bad loop_mode");
+    if (o.inner_precond != SCHUR_INNER_JACOBI && o.inner_precond != SCHUR_INNER_MG)
+        return set_error(SCHUR_EINVAL, "inner_precond must be SCHUR_INNER_JACOBI or SCHUR_INNER_MG");
     if (!(o.tol > 0) || !(o.tol_inner_A > 0) || !(o.tol_inner_S > 0) || o.max_outer < 1 ||
         o.max_inner < 1)
         return set_error(SCHUR_EINVAL, "tolerances must be > 0 and caps >= 1");
@@ -414,11 +419,24 @@ int prepare_solve(Handle& H, const schur_opts& opts, int use_graph) {
         const size_t nu = (size_t)std::max(H.n_u, 1ll), np = (size_t)std::max(H.n_p, 1ll);
         cudaError_t e = cudaSuccess;
         auto A = [&](float** p, size_t n) { if (e == cudaSuccess) e = alloc(H, p, n); };
-        A(&H.axf, nu); A(&H.arf, nu); A(&H.apf, nu + 1); A(&H.aqf, nu);
-        A(&H.sxf, np); A(&H.srf, np); A(&H.spf, np + 1); A(&H.sqf, np); A(&H.invdSf, np);
+        A(&H.axf, nu); A(&H.arf, nu + 1); A(&H.apf, nu + 1); A(&H.aqf, nu);
+        A(&H.sxf, np); A(&H.srf, np + 1); A(&H.spf, np + 1); A(&H.sqf, np); A(&H.invdSf, np);
         if (e == cudaSuccess) e = launch_to_float(H, H.invdSc, H.invdSf, (long long)np);
         if (e == cudaErrorMemoryAllocation) return set_error(SCHUR_ENOMEM, "device allocation failed");
         if (e != cudaSuccess) return cuda_error(e, "mixed-precision buffers");
+    }
+    // inner preconditioner: the recorded graphs embed it, so a change drops them; the
+    // multigrid hierarchies are built on first use (A always, S-hat for SIMPLE)
+    if (o.inner_precond != H.inner_precond) {
+        cudaStreamSynchronize(H.stream);  // recorded graphs may still run
+        drop_graphs(H);
+        H.inner_precond = o.inner_precond;
+    }
+    if (o.inner_precond == SCHUR_INNER_MG) {
+        const bool f32 = o.precision == SCHUR_MIXED;
+        int rc = mg_prepare(H, false, f32);
+        if (!rc && o.precond == SCHUR_SIMPLE) rc = mg_prepare(H, true, f32);
+        if (rc) return rc;
     }
     // per-iteration record of the outer loop, NaN-filled (all bytes 0xff) before the call
     const int need = std::min(std::max(o.max_outer, 1), kHistMax);
@@ -517,6 +535,7 @@ void schur_opts_default(schur_opts* o) {
     o->refine_factor = 1e-3;
     o->max_refine = 30;
     o->step_max = 1000;
+    o->inner_precond = SCHUR_INNER_JACOBI;
 }
 
 const char* schur_last_error(void) { return g_last_error.c_str(); }

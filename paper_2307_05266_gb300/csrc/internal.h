@@ -22,6 +22,24 @@ struct NvtxRange {
     NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// Multigrid hierarchy of one inner operator (A or S-hat_simple), built by mg.cu.  Level 0
+// is the fine operator in the compact layout; levels 1 .. nlev-1 are Galerkin operators of
+// 2 x 2 x 2 aggregates stored as 7-point tables, the last one diagonal.
+struct MgOp {
+    int nlev = 0;                  // levels including the fine one (0: not built)
+    int tail = 0;                  // first level that one block runs alone in the loop kernel
+    std::vector<long long> n;      // entries per level
+    std::vector<long long> ld;     // row stride of the 6- and 8-row tables per level
+    std::vector<uint32_t*> nb;     // [6][ld] neighbour entries (level >= 1)
+    std::vector<uint32_t*> ch;     // [8][ld] children at the level below (level >= 1)
+    std::vector<uint32_t*> agg;    // [n + 1] parent at the level above (all but the last)
+    std::vector<double*> w, dg, wd;  // FP64 values per level (level 0: wd only)
+    void* lev64 = nullptr;         // device array of FP64 level descriptors
+    void* lev32 = nullptr;         // FP32 descriptors (mixed precision, built on first use)
+    std::vector<void*> bufs;       // every device buffer of the hierarchy
+    long long bytes = 0;
+};
+
 // Device buffers and graphs of one geometry (the object behind schur_geom_t).
 struct Handle {
     Dev g{};
@@ -92,6 +110,11 @@ struct Handle {
     int next_slot = 0;
     std::vector<std::pair<int, unsigned long long>> handles;
 
+    // multigrid inner preconditioner: hierarchies of A and S-hat (built on first use) and
+    // the inner preconditioner of the recorded graphs (SCHUR_INNER_*)
+    MgOp mgA, mgS;
+    int inner_precond = 0;
+
     double force[3] = {1.0, 0.0, 0.0};
     bool solved = false, recovered = false;
     int last_loop = 0;
@@ -121,6 +144,15 @@ void record_recover(Handle& H, Recorder& R);
 void record_solve_recover(Handle& H, Recorder& R, int precond, int precision);
 void record_solve_A(Handle& H, Recorder& R, const double* b, double* x);
 cudaError_t time_kernel(Handle& H, int which, int slot, float* ms);
+
+// mg.cu: build the multigrid hierarchy of A (simple = false) or S-hat (simple = true) when
+// missing, and its FP32 values when fp32 is set (returns a SCHUR_* code); record the
+// persistent multigrid-preconditioned CG loop of one inner solve (after its init kernel);
+// free a hierarchy.
+int mg_prepare(Handle& H, bool simple, bool fp32);
+void record_mg_loop(Handle& H, Recorder& R, bool simple, bool fp32, void* x, void* r, void* p,
+                    void* q, CgState* st, const int* gate);
+void mg_free(MgOp& M);
 
 }  // namespace schur
 
