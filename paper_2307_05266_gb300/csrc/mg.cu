@@ -213,6 +213,7 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
     unsigned target = 0;
     bool ok = true;
     bool first_pass = true;
+    bool started = false;
     for (;;) {
         // ---- V-cycle on r (complete: written by the init kernel or before the barrier)
         if (!first_pass && !(ok = grid_barrier(ctl, target))) break;
@@ -281,11 +282,14 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
             v2[1] = (double)a1;
         }
         if (!(ok = grid_sum<2>(v2, P2, ctl, target))) break;
+        // the first cycle of the kernel starts the iteration (rho, ||z_0||); every later one
+        // ends an iteration (count, stop test, beta)
         if (threadIdx.x == 0) {
-            s_cont = s.first ? start_inner(nullptr, &s, v2[0], v2[1])
-                             : finish_inner(nullptr, &s, v2[0], v2[1]);
+            s_cont = started ? finish_inner(nullptr, &s, v2[0], v2[1])
+                             : start_inner(nullptr, &s, v2[0], v2[1]);
         }
         __syncthreads();
+        started = true;
         if (!s_cont) break;
         // ---- p = z + beta p (z was written by this thread: same mapping as above)
         {
