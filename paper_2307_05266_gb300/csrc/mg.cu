@@ -40,9 +40,10 @@ constexpr long long kMgTailMax = 1024;   // levels with at most this many entrie
 constexpr int kMgMaxLevels = 40;
 
 // Device descriptor of one level.  Every vector has one more entry, kept at 0, that the
-// sentinels of the tables point at (a missing neighbour, a missing child, the parent of the
-// sentinel).  Level 0: b is the CG residual r, out is the CG's z (in its q buffer), and the
-// operator comes from the fine tables (nb, ch, w, dg unused).
+// sentinels of the tables point at (a missing neighbour, a missing child).  Level 0: b is
+// the CG residual r, out is the CG's z (in its q buffer), and the operator comes from the
+// fine tables (nb, ch, w, dg unused).  res holds the residual after pre-smoothing on the way
+// down and, once the level above has used it, y = z + gamma P out_(l+1) on the way up.
 template <typename T>
 struct MgLev {
     uint32_t n, ld, nfine, ncoarse;
@@ -53,9 +54,9 @@ struct MgLev {
     const T* dg;          // [n] diagonal
     const T* wd;          // [n + 1] omega / diagonal (0: nullspace); last level: 1 / diagonal
     T* b;                 // [n + 1] right-hand side of the level
-    T* z;                 // [n + 1] pre-smoothed correction
-    T* res;               // [n + 1] residual after pre-smoothing
-    T* out;               // [n + 1] correction after post-smoothing
+    T* z;                 // [n + 1] pre-smoothed correction wd b
+    T* res;               // [n + 1] residual after pre-smoothing, then y
+    T* out;               // level 0: the cycle's output
 };
 
 template <typename T>
@@ -67,113 +68,108 @@ struct MgRun {
 
 // ---- per-entry work of one phase ----------------------------------------------------------
 
-// Fine operator of the compact layout applied at entry i: (Op y)_i with y_i = yi and y at a
-// neighbour j given by Y(j) (j = n for a missing neighbour; Y(n) = 0).
-template <typename T, bool kS, class Y>
+// Fine operator of the compact layout applied at entry i to a vector v with v_i = vi.
+template <typename T, bool kS>
 __device__ __forceinline__ T fine_apply(const Tabs<T>& t, const Dev& g, const Compact& C,
-                                        const T* __restrict__ dS, uint32_t i, T yi, const Y& y) {
+                                        const T* __restrict__ dS, uint32_t i, T vi,
+                                        const T* __restrict__ v) {
     const int ne = 2 * g.d;
     if constexpr (!kS) {
         const int gh = C.ufl[i] >> 1;
         T s = (T)0;
 #pragma unroll
         for (int e = 0; e < 6; ++e)
-            if (e < ne) s += y(__ldg(C.nbA + e * C.ldA + i));
-        return t.diag[gh] * yi - s;
+            if (e < ne) s += v[__ldg(C.nbA + e * C.ldA + i)];
+        return t.diag[gh] * vi - s;
     } else {
         const uint32_t code = __ldg(C.codeS + i);
         T s = (T)0;
         if constexpr (sizeof(T) == 8) {
 #pragma unroll
             for (int e = 0; e < 6; ++e)
-                if (e < ne) s += t.w[(code >> (3 * e)) & 7u] * y(__ldg(C.nbS + e * C.ldS + i));
-            return dS[i] * yi - s;
+                if (e < ne) s += t.w[(code >> (3 * e)) & 7u] * v[__ldg(C.nbS + e * C.ldS + i)];
+            return dS[i] * vi - s;
         } else {
 #pragma unroll
             for (int e = 0; e < 6; ++e)
-                if (e < ne) s += t.w[(code >> (3 * e)) & 7u] * (yi - y(__ldg(C.nbS + e * C.ldS + i)));
+                if (e < ne) s += t.w[(code >> (3 * e)) & 7u] * (vi - v[__ldg(C.nbS + e * C.ldS + i)]);
             return s;
         }
     }
 }
 
-// Fine level, down: z0 = wd0 r, res0 = r - Op z0 (z0 at a neighbour from r there).
+// Coarse operator of level L applied at entry i to v.
+template <typename T>
+__device__ __forceinline__ T coarse_apply(const MgLev<T>& L, uint32_t i, T vi, const T* __restrict__ v) {
+    T s = L.dg[i] * vi;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) s += L.w[e * L.ld + i] * v[__ldg(L.nb + e * L.ld + i)];
+    return s;
+}
+
+// Prolongation of the correction of entry i of level L to its children: y = z + gamma out
+// on the level below (written into that level's res buffer, whose residual is consumed).
+template <typename T>
+__device__ __forceinline__ void prolong_entry(const MgLev<T>& L, const T* __restrict__ zf,
+                                              T* __restrict__ yf, T gamma, T out, uint32_t i) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const uint32_t k = __ldg(L.ch + c * L.ld + i);
+        if (k < L.nfine) yf[k] = zf[k] + gamma * out;
+    }
+}
+
+// Fine level, down: res0 = r - Op z0 (z0 = wd0 r, formed with r).
 template <typename T, bool kS>
 __device__ __forceinline__ void mg_down_fine_entry(const Tabs<T>& t, const Dev& g, const Compact& C,
                                                    const T* __restrict__ dS, const MgLev<T>& L,
                                                    uint32_t i) {
-    const T* __restrict__ r = L.b;
-    const T* __restrict__ wd = L.wd;
-    const T ri = r[i];
-    const T zi = wd[i] * ri;
-    const T az = fine_apply<T, kS>(t, g, C, dS, i, zi, [&](uint32_t j) { return wd[j] * r[j]; });
-    L.z[i] = zi;
-    L.res[i] = ri - az;
+    const T* __restrict__ z = L.z;
+    L.res[i] = L.b[i] - fine_apply<T, kS>(t, g, C, dS, i, z[i], z);
 }
 
-// Fine level, up: z = y + wd0 (r - Op y), y = z0 + gamma out_1[agg0]; returns z (the CG's
-// preconditioned residual, stored in out = q).
+// Fine level, up: z = y + wd0 (r - Op y); returns z (the CG's preconditioned residual,
+// stored in out = q).
 template <typename T, bool kS>
 __device__ __forceinline__ T mg_up_fine_entry(const Tabs<T>& t, const Dev& g, const Compact& C,
                                               const T* __restrict__ dS, const MgLev<T>& L,
-                                              const T* __restrict__ outc, T gamma, uint32_t i) {
-    const T* __restrict__ z0 = L.z;
-    const uint32_t* __restrict__ agg = L.agg;
-    const T yi = z0[i] + gamma * outc[agg[i]];
-    const T ay = fine_apply<T, kS>(t, g, C, dS, i, yi,
-                                   [&](uint32_t j) { return z0[j] + gamma * outc[agg[j]]; });
-    const T zf = yi + L.wd[i] * (L.b[i] - ay);
+                                              uint32_t i) {
+    const T* __restrict__ y = L.res;
+    const T yi = y[i];
+    const T zf = yi + L.wd[i] * (L.b[i] - fine_apply<T, kS>(t, g, C, dS, i, yi, y));
     L.out[i] = zf;
     return zf;
 }
 
-// Coarse level, down: z = wd b, res = b - A z.
+// Coarse level, down: res = b - A z.
 template <typename T>
 __device__ __forceinline__ void mg_down_entry(const MgLev<T>& L, uint32_t i) {
-    const T* __restrict__ b = L.b;
-    const T* __restrict__ wd = L.wd;
-    const T bi = b[i];
-    const T zi = wd[i] * bi;
-    T az = L.dg[i] * zi;
-#pragma unroll
-    for (int e = 0; e < 6; ++e) {
-        const uint32_t j = __ldg(L.nb + e * L.ld + i);
-        az += L.w[e * L.ld + i] * (wd[j] * b[j]);
-    }
-    L.z[i] = zi;
-    L.res[i] = bi - az;
+    const T* __restrict__ z = L.z;
+    L.res[i] = L.b[i] - coarse_apply(L, i, z[i], z);
 }
 
-// Coarse level, restriction: b = sum of the children's residuals; on the last level also
-// its exact solve, z = out = wd b.
+// Coarse level, restriction: b = the sum of the children's residuals, z = wd b; on the last
+// level z is the exact solve and is prolonged at once.
 template <typename T>
-__device__ __forceinline__ void mg_restrict_entry(const MgLev<T>& L, const T* __restrict__ resf,
+__device__ __forceinline__ void mg_restrict_entry(const MgLev<T>& L, const MgLev<T>& F, T gamma,
                                                   bool last, uint32_t i) {
+    const T* __restrict__ resf = F.res;
     T s = (T)0;
 #pragma unroll
     for (int c = 0; c < 8; ++c) s += resf[__ldg(L.ch + c * L.ld + i)];
     L.b[i] = s;
-    if (last) {
-        const T zi = L.wd[i] * s;
-        L.z[i] = zi;
-        L.out[i] = zi;
-    }
+    const T zi = L.wd[i] * s;
+    L.z[i] = zi;
+    if (last) prolong_entry(L, (const T*)F.z, F.res, gamma, zi, i);
 }
 
-// Coarse level, up: out = y + wd (b - A y), y = z + gamma out_(l+1)[agg].
+// Coarse level, up: out = y + wd (b - A y), prolonged to the level below.
 template <typename T>
-__device__ __forceinline__ void mg_up_entry(const MgLev<T>& L, const T* __restrict__ outc, T gamma,
-                                            uint32_t i) {
-    const T* __restrict__ z = L.z;
-    const uint32_t* __restrict__ agg = L.agg;
-    const T yi = z[i] + gamma * outc[agg[i]];
-    T ay = L.dg[i] * yi;
-#pragma unroll
-    for (int e = 0; e < 6; ++e) {
-        const uint32_t j = __ldg(L.nb + e * L.ld + i);
-        ay += L.w[e * L.ld + i] * (z[j] + gamma * outc[agg[j]]);
-    }
-    L.out[i] = yi + L.wd[i] * (L.b[i] - ay);
+__device__ __forceinline__ void mg_up_entry(const MgLev<T>& L, const MgLev<T>& F, T gamma, uint32_t i) {
+    const T* __restrict__ y = L.res;
+    const T yi = y[i];
+    const T out = yi + L.wd[i] * (L.b[i] - coarse_apply(L, i, yi, y));
+    prolong_entry(L, (const T*)F.z, F.res, gamma, out, i);
 }
 
 // ---- loops over a level: the whole grid (grid-stride) or block 0 alone -----------------
@@ -182,16 +178,11 @@ __device__ __forceinline__ void mg_up_entry(const MgLev<T>& L, const T* __restri
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
 #define MG_BLOCK_LOOP(i, n) for (uint32_t i = threadIdx.x; i < (n); i += blockDim.x)
 
-template <typename T>
-__device__ __forceinline__ MgLev<T> mg_level(const MgRun<T>& M, int l) {
-    return M.lev[l];
-}
-
 // The multigrid-preconditioned CG loop of one inner solve, after its init kernel (x = 0,
-// r = b, status NOTCONV when b != 0).  aux: Jacobi weights of S-hat (unused here), dS: the
-// diagonal of S-hat (FP64 S stencil).  Same contract as the Jacobi loop kernels: all blocks
-// hold bitwise-equal scalars (block-identical grid sums), `gate` skips the solve, block 0
-// writes the final state, a failed barrier leaves ST_BARRIER.
+// r = b, status NOTCONV when b != 0).  dS: the diagonal of S-hat (FP64 S stencil).  Same
+// contract as the Jacobi loop kernels: all blocks hold bitwise-equal scalars (block-
+// identical grid sums), `gate` skips the solve, block 0 writes the final state, a failed
+// barrier leaves ST_BARRIER.
 template <typename T, bool kS>
 __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const MgRun<T>& M,
                                         const T* __restrict__ dS, T* __restrict__ xv,
@@ -210,28 +201,29 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
     double* P2 = partials + kMaxBlocks;  // [grid][2] r.z, z.z
     const int nlev = M.nlev, tail = M.tail;
     const T gamma = M.gamma;
+    const T* __restrict__ wd0 = M.lev[0].wd;
+    T* __restrict__ z0 = M.lev[0].z;
     unsigned target = 0;
     bool ok = true;
-    bool first_pass = true;
     bool started = false;
+    // z0 = wd0 r for the first cycle (later cycles form it with the r update)
+    MG_GRID_LOOP(i, n) z0[i] = wd0[i] * rv[i];
     for (;;) {
-        // ---- V-cycle on r (complete: written by the init kernel or before the barrier)
-        if (!first_pass && !(ok = grid_barrier(ctl, target))) break;
-        first_pass = false;
+        // ---- V-cycle on r (r and z0 complete after this barrier)
+        if (!(ok = grid_barrier(ctl, target))) break;
         {
-            const MgLev<T> L0 = mg_level(M, 0);
+            const MgLev<T> L0 = M.lev[0];
             MG_GRID_LOOP(i, n) mg_down_fine_entry<T, kS>(t, g, C, dS, L0, i);
         }
         if (!(ok = grid_barrier(ctl, target))) break;
         for (int l = 1; l < tail; ++l) {
             {
-                const MgLev<T> L = mg_level(M, l);
-                const T* resf = opaque(M.lev[l - 1].res);
-                MG_GRID_LOOP(i, L.n) mg_restrict_entry<T>(L, resf, false, i);
+                const MgLev<T> L = M.lev[l], F = M.lev[l - 1];
+                MG_GRID_LOOP(i, L.n) mg_restrict_entry<T>(L, F, gamma, false, i);
             }
             if (!(ok = grid_barrier(ctl, target))) break;
             {
-                const MgLev<T> L = mg_level(M, l);
+                const MgLev<T> L = M.lev[l];
                 MG_GRID_LOOP(i, L.n) mg_down_entry<T>(L, i);
             }
             if (!(ok = grid_barrier(ctl, target))) break;
@@ -239,10 +231,9 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
         if (!ok) break;
         if (blockIdx.x == 0) {
             for (int l = tail; l < nlev; ++l) {
-                const MgLev<T> L = mg_level(M, l);
-                const T* resf = opaque(M.lev[l - 1].res);
+                const MgLev<T> L = M.lev[l], F = M.lev[l - 1];
                 const bool last = (l == nlev - 1);
-                MG_BLOCK_LOOP(i, L.n) mg_restrict_entry<T>(L, resf, last, i);
+                MG_BLOCK_LOOP(i, L.n) mg_restrict_entry<T>(L, F, gamma, last, i);
                 __syncthreads();
                 if (!last) {
                     MG_BLOCK_LOOP(i, L.n) mg_down_entry<T>(L, i);
@@ -250,18 +241,16 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
                 }
             }
             for (int l = nlev - 2; l >= tail; --l) {
-                const MgLev<T> L = mg_level(M, l);
-                const T* outc = opaque(M.lev[l + 1].out);
-                MG_BLOCK_LOOP(i, L.n) mg_up_entry<T>(L, outc, gamma, i);
+                const MgLev<T> L = M.lev[l], F = M.lev[l - 1];
+                MG_BLOCK_LOOP(i, L.n) mg_up_entry<T>(L, F, gamma, i);
                 __syncthreads();
             }
         }
         if (!(ok = grid_barrier(ctl, target))) break;
         for (int l = tail - 1; l >= 1; --l) {
             {
-                const MgLev<T> L = mg_level(M, l);
-                const T* outc = opaque(M.lev[l + 1].out);
-                MG_GRID_LOOP(i, L.n) mg_up_entry<T>(L, outc, gamma, i);
+                const MgLev<T> L = M.lev[l], F = M.lev[l - 1];
+                MG_GRID_LOOP(i, L.n) mg_up_entry<T>(L, F, gamma, i);
             }
             if (!(ok = grid_barrier(ctl, target))) break;
         }
@@ -269,13 +258,11 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
         // ---- z = the cycle's output (in q), r.z and z.z
         double v2[2];
         {
-            const MgLev<T> L0 = mg_level(M, 0);
-            const T* outc = opaque(M.lev[1].out);
+            const MgLev<T> L0 = M.lev[0];
             T a0 = (T)0, a1 = (T)0;
             MG_GRID_LOOP(i, n) {
-                const T zf = mg_up_fine_entry<T, kS>(t, g, C, dS, L0, outc, gamma, i);
-                const T ri = rv[i];
-                a0 += ri * zf;
+                const T zf = mg_up_fine_entry<T, kS>(t, g, C, dS, L0, i);
+                a0 += rv[i] * zf;
                 a1 += zf * zf;
             }
             v2[0] = (double)a0;
@@ -291,7 +278,7 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
         __syncthreads();
         started = true;
         if (!s_cont) break;
-        // ---- p = z + beta p (z was written by this thread: same mapping as above)
+        // ---- p = z + beta p
         {
             const T beta = (T)(s.first ? 0.0 : s.beta);
             T* __restrict__ p = opaque(pv);
@@ -320,16 +307,20 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
         }
         __syncthreads();
         if (!s_cont) break;
-        // ---- x += alpha p, r -= alpha q
+        // ---- x += alpha p, r -= alpha q, z0 = wd0 r (the first smoothing step)
         {
             const T alpha = (T)s.alpha;
             T* __restrict__ x = opaque(xv);
             T* __restrict__ r = opaque(rv);
             const T* __restrict__ p = opaque(pv);
             const T* __restrict__ q = opaque(qv);
+            const T* __restrict__ w0 = opaque(wd0);
+            T* __restrict__ zz = opaque(z0);
             MG_GRID_LOOP(i, n) {
                 x[i] += alpha * p[i];
-                r[i] -= alpha * q[i];
+                const T ri = r[i] - alpha * q[i];
+                r[i] = ri;
+                zz[i] = w0[i] * ri;
             }
         }
     }
@@ -605,7 +596,6 @@ int build_descriptors(Handle& H, MgOp& M, bool simple, void** out) {
             v.out = simple ? (f32 ? (T*)H.sqf : (T*)H.sq) : (f32 ? (T*)H.aqf : (T*)H.aq);
         } else {
             vec(M.n[l] + 1, &v.b);
-            vec(M.n[l] + 1, &v.out);
         }
         vec(M.n[l] + 1, &v.z);
         vec(M.n[l] + 1, &v.res);
