@@ -433,9 +433,8 @@ int prepare_solve(Handle& H, const schur_opts& opts, int use_graph) {
         H.inner_precond = o.inner_precond;
     }
     if (o.inner_precond == SCHUR_INNER_MG) {
-        const bool f32 = o.precision == SCHUR_MIXED;
-        int rc = mg_prepare(H, false, f32);
-        if (!rc && o.precond == SCHUR_SIMPLE) rc = mg_prepare(H, true, f32);
+        int rc = mg_prepare(H, false);
+        if (!rc && o.precond == SCHUR_SIMPLE) rc = mg_prepare(H, true);
         if (rc) return rc;
     }
     // per-iteration record of the outer loop, NaN-filled (all bytes 0xff) before the call

@@ -29,13 +29,8 @@ struct MgOp {
     int nlev = 0;                  // levels including the fine one (0: not built)
     int tail = 0;                  // first level that one block runs alone in the loop kernel
     std::vector<long long> n;      // entries per level
-    std::vector<long long> ld;     // row stride of the 6- and 8-row tables per level
-    std::vector<uint32_t*> nb;     // [6][ld] neighbour entries (level >= 1)
-    std::vector<uint32_t*> ch;     // [8][ld] children at the level below (level >= 1)
-    std::vector<uint32_t*> agg;    // [n + 1] parent at the level above (all but the last)
-    std::vector<double*> w, dg, wd;  // FP64 values per level (level 0: wd only)
-    void* lev64 = nullptr;         // device array of FP64 level descriptors
-    void* lev32 = nullptr;         // FP32 descriptors (mixed precision, built on first use)
+    void* lev = nullptr;           // device array of the levels' descriptors (FP32 cycle)
+    float* r32 = nullptr;          // [n_0 + 1] FP32 copy of an FP64 inner residual
     std::vector<void*> bufs;       // every device buffer of the hierarchy
     long long bytes = 0;
 };
@@ -146,10 +141,10 @@ void record_solve_A(Handle& H, Recorder& R, const double* b, double* x);
 cudaError_t time_kernel(Handle& H, int which, int slot, float* ms);
 
 // mg.cu: build the multigrid hierarchy of A (simple = false) or S-hat (simple = true) when
-// missing, and its FP32 values when fp32 is set (returns a SCHUR_* code); record the
+// missing (returns a SCHUR_* code); record the
 // persistent multigrid-preconditioned CG loop of one inner solve (after its init kernel);
 // free a hierarchy.
-int mg_prepare(Handle& H, bool simple, bool fp32);
+int mg_prepare(Handle& H, bool simple);
 void record_mg_loop(Handle& H, Recorder& R, bool simple, bool fp32, void* x, void* r, void* p,
                     void* q, CgState* st, const int* gate);
 void mg_free(MgOp& M);

@@ -11,22 +11,27 @@
 //   the couplings that stay inside).  Levels are added until the grid is a single cell;
 //   that last matrix is diagonal and is solved exactly by its pseudo-inverse.  A diagonal
 //   at most 1e-12 times the entry's diagonal mass (the sum of the fine diagonals it
-//   aggregates) counts as zero: the entry is a nullspace unknown with weight 0.
-// V-cycle (from x = 0, on the residual r of the CG): z_l = omega D^-1 b_l and the residual
-//   res_l = b_l - A_l z_l (one stencil on b), b_(l+1) = P^T res_l (a gather over the 8
-//   children), the coarse correction scaled by gamma, and one Jacobi sweep after:
-//   out_l = y + omega D^-1 (b_l - A_l y), y = z_l + gamma P out_(l+1) (one stencil whose
-//   neighbour values are z at the neighbour plus the correction of its parent).  omega =
-//   0.9; gamma = 1.3 (A) and 1.7 (S-hat).  The cycle is symmetric positive definite, the
-//   CG stop rule is ||M^-1 r_k|| / ||M^-1 r_0|| < eps as for Jacobi, and the S-hat cycle's
-//   output is not projected (r stays in the range; the solution is projected afterwards).
-// Launch: one persistent cooperative kernel per inner solve.  The fine and the larger
-//   coarse levels run on the whole grid with a grid barrier between phases; the levels
-//   from `tail` down (at most kMgTailMax entries) run in block 0 alone with block barriers,
-//   while the other blocks wait at one grid barrier.  Per CG iteration: matvec + p.q, the
-//   x/r update, the V-cycle, z and the dots r.z, z.z, the direction update: 3 tail + 3 grid
-//   barriers.  Every grid wait is bounded (grid_barrier).
+//   aggregates) counts as zero: the entry is a nullspace unknown with weight 0.  The
+//   coefficients are summed in FP64 on the host and stored in FP32.
+// V-cycle (from x = 0, on the residual r of the CG), in FP32 for both CG precisions: the
+//   preconditioner only has to approximate A^-1 (its rounding perturbs the search
+//   directions by about 1e-7 relative, while the CG's iterates, residual updates, dot
+//   products and stop test stay in the CG's own precision).  Per level: z = omega D^-1 b
+//   (formed with b), res = b - A z (one stencil on z), b_(l+1) = P^T res (a gather over the
+//   8 children), the coarse correction scaled by gamma (over-correction), and one Jacobi
+//   sweep after: out = y + omega D^-1 (b - A y) with y = z + gamma P out_(l+1), which the
+//   parent writes into the level's res buffer once that residual is consumed.  omega = 0.9;
+//   gamma = 1.3 (A) and 1.7 (S-hat).  The cycle is symmetric positive definite; the CG stop
+//   rule is ||M^-1 r_k|| / ||M^-1 r_0|| < eps as for Jacobi, and the S-hat cycle's output is
+//   not projected (r stays in the range; the solution is projected afterwards).
+// Launch: one persistent cooperative kernel per inner solve.  The fine level and the large
+//   coarse levels run on the whole grid with a grid barrier after each phase; on coarse
+//   levels of at most kMgFuseMax entries the restriction and the down stencil are one phase
+//   (each entry re-forms b at its neighbours from their children); the levels from `tail`
+//   down (at most kMgTailMax entries) run in block 0 alone with block barriers while the
+//   other blocks wait at one grid barrier.  Every grid wait is bounded (grid_barrier).
 #include <cstring>
+#include <type_traits>
 
 #include "cg_dev.cuh"
 
@@ -36,140 +41,144 @@ constexpr double kMgOmega = 0.9;
 constexpr double kMgGammaA = 1.3;
 constexpr double kMgGammaS = 1.7;
 constexpr double kMgZeroDiag = 1e-12;
-constexpr long long kMgTailMax = 1024;   // levels with at most this many entries: block 0
+constexpr long long kMgTailMax = 1024;     // levels with at most this many entries: block 0
+constexpr long long kMgFuseMax = 131072;   // restriction fused into the down stencil
 constexpr int kMgMaxLevels = 40;
 
-// Device descriptor of one level.  Every vector has one more entry, kept at 0, that the
-// sentinels of the tables point at (a missing neighbour, a missing child).  Level 0: b is
-// the CG residual r, out is the CG's z (in its q buffer), and the operator comes from the
-// fine tables (nb, ch, w, dg unused).  res holds the residual after pre-smoothing on the way
-// down and, once the level above has used it, y = z + gamma P out_(l+1) on the way up.
-template <typename T>
+// Device descriptor of one level (FP32).  Every vector has one more entry, kept at 0, that
+// the sentinels of the tables point at (a missing neighbour, a missing child).  Level 0: b
+// is the FP32 copy of an FP64 CG residual (the kernel reads the FP32 residual it is given),
+// and the operator comes from the fine tables (nb, ch, w, dg unused).  res holds the residual after pre-smoothing on the way down and, once the
+// level above has consumed it, y = z + gamma P out_(l+1) on the way up.
 struct MgLev {
-    uint32_t n, ld, nfine, ncoarse;
+    uint32_t n, ld, nfine, fused;
     const uint32_t* nb;   // [6][ld] neighbour entry per direction, n = none
     const uint32_t* ch;   // [8][ld] children at level l - 1, nfine = none
-    const uint32_t* agg;  // [n + 1] parent at level l + 1 (agg[n] = ncoarse)
-    const T* w;           // [6][ld] off-diagonal coefficients (0 at missing neighbours)
-    const T* dg;          // [n] diagonal
-    const T* wd;          // [n + 1] omega / diagonal (0: nullspace); last level: 1 / diagonal
-    T* b;                 // [n + 1] right-hand side of the level
-    T* z;                 // [n + 1] pre-smoothed correction wd b
-    T* res;               // [n + 1] residual after pre-smoothing, then y
-    T* out;               // level 0: the cycle's output
+    const float* w;       // [6][ld] off-diagonal coefficients (0 at missing neighbours)
+    const float* dg;      // [n] diagonal
+    const float* wd;      // [n + 1] omega / diagonal (0: nullspace); last level: 1 / diagonal
+    float* b;             // [n + 1] right-hand side of the level
+    float* z;             // [n + 1] pre-smoothed correction wd b
+    float* res;           // [n + 1] residual after pre-smoothing, then y
 };
 
-template <typename T>
 struct MgRun {
-    const MgLev<T>* lev;  // [nlev] device descriptors
+    const MgLev* lev;     // [nlev] device descriptors
     int nlev, tail;
-    T gamma;
+    float gamma;
 };
 
 // ---- per-entry work of one phase ----------------------------------------------------------
 
-// Fine operator of the compact layout applied at entry i to a vector v with v_i = vi.
-template <typename T, bool kS>
-__device__ __forceinline__ T fine_apply(const Tabs<T>& t, const Dev& g, const Compact& C,
-                                        const T* __restrict__ dS, uint32_t i, T vi,
-                                        const T* __restrict__ v) {
+// Fine operator of the compact layout (FP32) applied at entry i to a vector v, v_i = vi.
+template <bool kS>
+__device__ __forceinline__ float fine_apply(const Tabs<float>& t, const Dev& g, const Compact& C,
+                                            uint32_t i, float vi, const float* __restrict__ v) {
     const int ne = 2 * g.d;
+    float s = 0.0f;
     if constexpr (!kS) {
         const int gh = C.ufl[i] >> 1;
-        T s = (T)0;
 #pragma unroll
         for (int e = 0; e < 6; ++e)
             if (e < ne) s += v[__ldg(C.nbA + e * C.ldA + i)];
         return t.diag[gh] * vi - s;
     } else {
         const uint32_t code = __ldg(C.codeS + i);
-        T s = (T)0;
-        if constexpr (sizeof(T) == 8) {
 #pragma unroll
-            for (int e = 0; e < 6; ++e)
-                if (e < ne) s += t.w[(code >> (3 * e)) & 7u] * v[__ldg(C.nbS + e * C.ldS + i)];
-            return dS[i] * vi - s;
-        } else {
-#pragma unroll
-            for (int e = 0; e < 6; ++e)
-                if (e < ne) s += t.w[(code >> (3 * e)) & 7u] * (vi - v[__ldg(C.nbS + e * C.ldS + i)]);
-            return s;
-        }
+        for (int e = 0; e < 6; ++e)
+            if (e < ne) s += t.w[(code >> (3 * e)) & 7u] * (vi - v[__ldg(C.nbS + e * C.ldS + i)]);
+        return s;
     }
 }
 
 // Coarse operator of level L applied at entry i to v.
-template <typename T>
-__device__ __forceinline__ T coarse_apply(const MgLev<T>& L, uint32_t i, T vi, const T* __restrict__ v) {
-    T s = L.dg[i] * vi;
+__device__ __forceinline__ float coarse_apply(const MgLev& L, uint32_t i, float vi,
+                                              const float* __restrict__ v) {
+    float s = L.dg[i] * vi;
 #pragma unroll
     for (int e = 0; e < 6; ++e) s += L.w[e * L.ld + i] * v[__ldg(L.nb + e * L.ld + i)];
     return s;
 }
 
-// Prolongation of the correction of entry i of level L to its children: y = z + gamma out
-// on the level below (written into that level's res buffer, whose residual is consumed).
-template <typename T>
-__device__ __forceinline__ void prolong_entry(const MgLev<T>& L, const T* __restrict__ zf,
-                                              T* __restrict__ yf, T gamma, T out, uint32_t i) {
+// b at entry i of level L: the sum of its children's residuals.
+__device__ __forceinline__ float restrict_at(const MgLev& L, const float* __restrict__ resf, uint32_t i) {
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += resf[__ldg(L.ch + c * L.ld + i)];
+    return s;
+}
+
+// Prolongation of the correction `out` of entry i of level L to its children: y = z + gamma
+// out on the level below F (written into F's res buffer, whose residual is consumed).
+__device__ __forceinline__ void prolong_entry(const MgLev& L, const MgLev& F, float gamma, float out,
+                                              uint32_t i) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const uint32_t k = __ldg(L.ch + c * L.ld + i);
-        if (k < L.nfine) yf[k] = zf[k] + gamma * out;
+        if (k < L.nfine) F.res[k] = F.z[k] + gamma * out;
     }
 }
 
-// Fine level, down: res0 = r - Op z0 (z0 = wd0 r, formed with r).
-template <typename T, bool kS>
-__device__ __forceinline__ void mg_down_fine_entry(const Tabs<T>& t, const Dev& g, const Compact& C,
-                                                   const T* __restrict__ dS, const MgLev<T>& L,
-                                                   uint32_t i) {
-    const T* __restrict__ z = L.z;
-    L.res[i] = L.b[i] - fine_apply<T, kS>(t, g, C, dS, i, z[i], z);
+// Fine level, down: res0 = b0 - Op z0.
+template <bool kS>
+__device__ __forceinline__ void mg_down_fine_entry(const Tabs<float>& t, const Dev& g,
+                                                   const Compact& C, const MgLev& L, uint32_t i) {
+    const float* __restrict__ z = L.z;
+    L.res[i] = L.b[i] - fine_apply<kS>(t, g, C, i, z[i], z);
 }
 
-// Fine level, up: z = y + wd0 (r - Op y); returns z (the CG's preconditioned residual,
-// stored in out = q).
-template <typename T, bool kS>
-__device__ __forceinline__ T mg_up_fine_entry(const Tabs<T>& t, const Dev& g, const Compact& C,
-                                              const T* __restrict__ dS, const MgLev<T>& L,
-                                              uint32_t i) {
-    const T* __restrict__ y = L.res;
-    const T yi = y[i];
-    const T zf = yi + L.wd[i] * (L.b[i] - fine_apply<T, kS>(t, g, C, dS, i, yi, y));
-    L.out[i] = zf;
-    return zf;
+// Fine level, up: z = y + wd0 (b0 - Op y), the cycle's output.
+template <bool kS>
+__device__ __forceinline__ float mg_up_fine_entry(const Tabs<float>& t, const Dev& g,
+                                                  const Compact& C, const MgLev& L, uint32_t i) {
+    const float* __restrict__ y = L.res;
+    const float yi = y[i];
+    return yi + L.wd[i] * (L.b[i] - fine_apply<kS>(t, g, C, i, yi, y));
 }
 
-// Coarse level, down: res = b - A z.
-template <typename T>
-__device__ __forceinline__ void mg_down_entry(const MgLev<T>& L, uint32_t i) {
-    const T* __restrict__ z = L.z;
+// Coarse level, restriction alone: b = P^T res_(l-1), z = wd b.
+__device__ __forceinline__ void mg_restrict_entry(const MgLev& L, const MgLev& F, uint32_t i) {
+    const float bi = restrict_at(L, F.res, i);
+    L.b[i] = bi;
+    L.z[i] = L.wd[i] * bi;
+}
+
+// Coarse level, down stencil alone: res = b - A z.
+__device__ __forceinline__ void mg_down_entry(const MgLev& L, uint32_t i) {
+    const float* __restrict__ z = L.z;
     L.res[i] = L.b[i] - coarse_apply(L, i, z[i], z);
 }
 
-// Coarse level, restriction: b = the sum of the children's residuals, z = wd b; on the last
-// level z is the exact solve and is prolonged at once.
-template <typename T>
-__device__ __forceinline__ void mg_restrict_entry(const MgLev<T>& L, const MgLev<T>& F, T gamma,
-                                                  bool last, uint32_t i) {
-    const T* __restrict__ resf = F.res;
-    T s = (T)0;
+// Coarse level, restriction and down stencil in one phase: b and z are re-formed at the
+// neighbours from their children.
+__device__ __forceinline__ void mg_restrict_down_entry(const MgLev& L, const MgLev& F, uint32_t i) {
+    const float* __restrict__ resf = F.res;
+    const float bi = restrict_at(L, resf, i);
+    const float zi = L.wd[i] * bi;
+    float s = L.dg[i] * zi;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) s += resf[__ldg(L.ch + c * L.ld + i)];
-    L.b[i] = s;
-    const T zi = L.wd[i] * s;
+    for (int e = 0; e < 6; ++e) {
+        const uint32_t j = __ldg(L.nb + e * L.ld + i);
+        s += L.w[e * L.ld + i] * (L.wd[j] * restrict_at(L, resf, j));
+    }
+    L.b[i] = bi;
     L.z[i] = zi;
-    if (last) prolong_entry(L, (const T*)F.z, F.res, gamma, zi, i);
+    L.res[i] = bi - s;
+}
+
+// Last level: restriction, exact solve z = wd b, prolongation.
+__device__ __forceinline__ void mg_last_entry(const MgLev& L, const MgLev& F, float gamma, uint32_t i) {
+    const float zi = L.wd[i] * restrict_at(L, F.res, i);
+    L.z[i] = zi;
+    prolong_entry(L, F, gamma, zi, i);
 }
 
 // Coarse level, up: out = y + wd (b - A y), prolonged to the level below.
-template <typename T>
-__device__ __forceinline__ void mg_up_entry(const MgLev<T>& L, const MgLev<T>& F, T gamma, uint32_t i) {
-    const T* __restrict__ y = L.res;
-    const T yi = y[i];
-    const T out = yi + L.wd[i] * (L.b[i] - coarse_apply(L, i, yi, y));
-    prolong_entry(L, (const T*)F.z, F.res, gamma, out, i);
+__device__ __forceinline__ void mg_up_entry(const MgLev& L, const MgLev& F, float gamma, uint32_t i) {
+    const float* __restrict__ y = L.res;
+    const float yi = y[i];
+    const float out = yi + L.wd[i] * (L.b[i] - coarse_apply(L, i, yi, y));
+    prolong_entry(L, F, gamma, out, i);
 }
 
 // ---- loops over a level: the whole grid (grid-stride) or block 0 alone -----------------
@@ -178,21 +187,26 @@ __device__ __forceinline__ void mg_up_entry(const MgLev<T>& L, const MgLev<T>& F
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
 #define MG_BLOCK_LOOP(i, n) for (uint32_t i = threadIdx.x; i < (n); i += blockDim.x)
 
-// The multigrid-preconditioned CG loop of one inner solve, after its init kernel (x = 0,
-// r = b, status NOTCONV when b != 0).  dS: the diagonal of S-hat (FP64 S stencil).  Same
+// The multigrid-preconditioned CG loop of one inner solve in precision T, after its init
+// kernel (x = 0, r = b, status NOTCONV when b != 0).  r32: the FP32 copy of r that the cycle
+// reads (r itself when T is float).  dS: the diagonal of S-hat (FP64 S stencil).  Same
 // contract as the Jacobi loop kernels: all blocks hold bitwise-equal scalars (block-
 // identical grid sums), `gate` skips the solve, block 0 writes the final state, a failed
 // barrier leaves ST_BARRIER.
 template <typename T, bool kS>
-__device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const MgRun<T>& M,
+__device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const MgRun& M,
                                         const T* __restrict__ dS, T* __restrict__ xv,
                                         T* __restrict__ rv, T* __restrict__ pv, T* __restrict__ qv,
-                                        Ctl* ctl, CgState* st, double* partials, const int* gate) {
+                                        float* __restrict__ r32, Ctl* ctl, CgState* st,
+                                        double* partials, const int* gate) {
+    constexpr bool kSame = std::is_same<T, float>::value;
     __shared__ CgState s;
     __shared__ unsigned s_cont;
     __shared__ Tabs<T> t;
+    __shared__ Tabs<float> tf;
     if (gate && *gate) return;
     load_tabs<T>(g, t);
+    load_tabs<float>(g, tf);
     if (threadIdx.x == 0) s = *st;
     __syncthreads();
     if (s.status != ST_NOTCONV || ld_acquire_u32(&ctl->bar_err) != 0u) return;
@@ -200,68 +214,74 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
     double* P1 = partials;               // [grid] p.q
     double* P2 = partials + kMaxBlocks;  // [grid][2] r.z, z.z
     const int nlev = M.nlev, tail = M.tail;
-    const T gamma = M.gamma;
-    const T* __restrict__ wd0 = M.lev[0].wd;
-    T* __restrict__ z0 = M.lev[0].z;
+    const float gamma = M.gamma;
     unsigned target = 0;
     bool ok = true;
     bool started = false;
-    // z0 = wd0 r for the first cycle (later cycles form it with the r update)
-    MG_GRID_LOOP(i, n) z0[i] = wd0[i] * rv[i];
+    {   // the FP32 residual and z0 = wd0 r for the first cycle (later: with the r update)
+        const float* __restrict__ wd0 = M.lev[0].wd;
+        float* __restrict__ z0 = M.lev[0].z;
+        MG_GRID_LOOP(i, n) {
+            const float ri = (float)rv[i];
+            if constexpr (!kSame) r32[i] = ri;
+            z0[i] = wd0[i] * ri;
+        }
+    }
     for (;;) {
-        // ---- V-cycle on r (r and z0 complete after this barrier)
+        // ---- V-cycle on r (r32 and z0 complete after this barrier)
         if (!(ok = grid_barrier(ctl, target))) break;
         {
-            const MgLev<T> L0 = M.lev[0];
-            MG_GRID_LOOP(i, n) mg_down_fine_entry<T, kS>(t, g, C, dS, L0, i);
+            MgLev L0 = M.lev[0];
+            L0.b = r32;
+            MG_GRID_LOOP(i, n) mg_down_fine_entry<kS>(tf, g, C, L0, i);
         }
         if (!(ok = grid_barrier(ctl, target))) break;
         for (int l = 1; l < tail; ++l) {
-            {
-                const MgLev<T> L = M.lev[l], F = M.lev[l - 1];
-                MG_GRID_LOOP(i, L.n) mg_restrict_entry<T>(L, F, gamma, false, i);
-            }
-            if (!(ok = grid_barrier(ctl, target))) break;
-            {
-                const MgLev<T> L = M.lev[l];
-                MG_GRID_LOOP(i, L.n) mg_down_entry<T>(L, i);
+            const MgLev L = M.lev[l], F = M.lev[l - 1];
+            if (L.fused) {
+                MG_GRID_LOOP(i, L.n) mg_restrict_down_entry(L, F, i);
+            } else {
+                MG_GRID_LOOP(i, L.n) mg_restrict_entry(L, F, i);
+                if (!(ok = grid_barrier(ctl, target))) break;
+                MG_GRID_LOOP(i, L.n) mg_down_entry(L, i);
             }
             if (!(ok = grid_barrier(ctl, target))) break;
         }
         if (!ok) break;
         if (blockIdx.x == 0) {
             for (int l = tail; l < nlev; ++l) {
-                const MgLev<T> L = M.lev[l], F = M.lev[l - 1];
-                const bool last = (l == nlev - 1);
-                MG_BLOCK_LOOP(i, L.n) mg_restrict_entry<T>(L, F, gamma, last, i);
-                __syncthreads();
-                if (!last) {
-                    MG_BLOCK_LOOP(i, L.n) mg_down_entry<T>(L, i);
-                    __syncthreads();
+                const MgLev L = M.lev[l], F = M.lev[l - 1];
+                if (l == nlev - 1) {
+                    MG_BLOCK_LOOP(i, L.n) mg_last_entry(L, F, gamma, i);
+                } else {
+                    MG_BLOCK_LOOP(i, L.n) mg_restrict_down_entry(L, F, i);
                 }
+                __syncthreads();
             }
             for (int l = nlev - 2; l >= tail; --l) {
-                const MgLev<T> L = M.lev[l], F = M.lev[l - 1];
-                MG_BLOCK_LOOP(i, L.n) mg_up_entry<T>(L, F, gamma, i);
+                const MgLev L = M.lev[l], F = M.lev[l - 1];
+                MG_BLOCK_LOOP(i, L.n) mg_up_entry(L, F, gamma, i);
                 __syncthreads();
             }
         }
         if (!(ok = grid_barrier(ctl, target))) break;
         for (int l = tail - 1; l >= 1; --l) {
             {
-                const MgLev<T> L = M.lev[l], F = M.lev[l - 1];
-                MG_GRID_LOOP(i, L.n) mg_up_entry<T>(L, F, gamma, i);
+                const MgLev L = M.lev[l], F = M.lev[l - 1];
+                MG_GRID_LOOP(i, L.n) mg_up_entry(L, F, gamma, i);
             }
             if (!(ok = grid_barrier(ctl, target))) break;
         }
         if (!ok) break;
-        // ---- z = the cycle's output (in q), r.z and z.z
+        // ---- z = the cycle's output (into q), r.z and z.z
         double v2[2];
         {
-            const MgLev<T> L0 = M.lev[0];
+            MgLev L0 = M.lev[0];
+            L0.b = r32;
             T a0 = (T)0, a1 = (T)0;
             MG_GRID_LOOP(i, n) {
-                const T zf = mg_up_fine_entry<T, kS>(t, g, C, dS, L0, i);
+                const T zf = (T)mg_up_fine_entry<kS>(tf, g, C, L0, i);
+                qv[i] = zf;
                 a0 += rv[i] * zf;
                 a1 += zf * zf;
             }
@@ -307,20 +327,23 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
         }
         __syncthreads();
         if (!s_cont) break;
-        // ---- x += alpha p, r -= alpha q, z0 = wd0 r (the first smoothing step)
+        // ---- x += alpha p, r -= alpha q, the FP32 residual and z0 = wd0 r
         {
             const T alpha = (T)s.alpha;
             T* __restrict__ x = opaque(xv);
             T* __restrict__ r = opaque(rv);
             const T* __restrict__ p = opaque(pv);
             const T* __restrict__ q = opaque(qv);
-            const T* __restrict__ w0 = opaque(wd0);
-            T* __restrict__ zz = opaque(z0);
+            const float* __restrict__ w0 = opaque(M.lev[0].wd);
+            float* __restrict__ z0 = opaque(M.lev[0].z);
+            float* __restrict__ rf = opaque(r32);
             MG_GRID_LOOP(i, n) {
                 x[i] += alpha * p[i];
                 const T ri = r[i] - alpha * q[i];
                 r[i] = ri;
-                zz[i] = w0[i] * ri;
+                const float r32i = (float)ri;
+                if constexpr (!kSame) rf[i] = r32i;
+                z0[i] = w0[i] * r32i;
             }
         }
     }
@@ -332,13 +355,14 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
 }
 
 template <typename T, bool kS>
-__global__ void __launch_bounds__(kBlock, 3) k_mg_loop(Dev g, Compact C, MgRun<T> M,
+__global__ void __launch_bounds__(kBlock, 3) k_mg_loop(Dev g, Compact C, MgRun M,
                                                        const T* __restrict__ dS, T* __restrict__ xv,
                                                        T* __restrict__ rv, T* __restrict__ pv,
-                                                       T* __restrict__ qv, Ctl* ctl, CgState* st,
-                                                       double* partials, const int* gate) {
+                                                       T* __restrict__ qv, float* __restrict__ r32,
+                                                       Ctl* ctl, CgState* st, double* partials,
+                                                       const int* gate) {
     count_launch(ctl);
-    mg_loop<T, kS>(g, C, M, dS, xv, rv, pv, qv, ctl, st, partials, gate);
+    mg_loop<T, kS>(g, C, M, dS, xv, rv, pv, qv, r32, ctl, st, partials, gate);
 }
 
 // ---- hierarchy build (host) ---------------------------------------------------------------
@@ -536,80 +560,15 @@ bool single_cell(const HostLevel& L) {
 
 // Weights of the smoother (omega / diagonal) or, on the last level, of the exact solve
 // (1 / diagonal); 0 for a diagonal that counts as zero; one more entry (0) for the sentinel.
-std::vector<double> weights(const HostLevel& L, double scale) {
-    std::vector<double> wd((size_t)L.n + 1, 0.0);
+std::vector<float> weights(const HostLevel& L, double scale) {
+    std::vector<float> wd((size_t)L.n + 1, 0.0f);
     for (long long i = 0; i < L.n; ++i)
-        if (L.dg[i] > kMgZeroDiag * L.mass[i]) wd[i] = scale / L.dg[i];
+        if (L.dg[i] > kMgZeroDiag * L.mass[i]) wd[i] = (float)(scale / L.dg[i]);
     return wd;
 }
 
-template <typename T>
-__global__ void k_mg_convert(const double* __restrict__ src, T* __restrict__ dst, long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        dst[i] = (T)src[i];
-}
-
-// Device descriptors of precision T over the hierarchy's tables (FP32 values converted from
-// the FP64 ones; vectors allocated per precision).
-template <typename T>
-int build_descriptors(Handle& H, MgOp& M, bool simple, void** out) {
-    const int L = M.nlev;
-    const cudaStream_t s = H.stream;
-    std::vector<MgLev<T>> d((size_t)L);
-    cudaError_t e = cudaSuccess;
-    auto conv = [&](const double* src, long long n, const T** dst) {
-        if (e != cudaSuccess) return;
-        if (sizeof(T) == sizeof(double)) {
-            *dst = (const T*)src;
-            return;
-        }
-        T* p = nullptr;
-        e = mg_alloc(M, s, &p, (size_t)n);
-        if (e != cudaSuccess) return;
-        k_mg_convert<T><<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(src, p, n);
-        e = cudaGetLastError();
-        *dst = p;
-    };
-    auto vec = [&](long long n, T** dst) {
-        if (e == cudaSuccess) e = mg_alloc(M, s, dst, (size_t)n);
-    };
-    const bool f32 = sizeof(T) == sizeof(float);
-    for (int l = 0; l < L; ++l) {
-        MgLev<T>& v = d[l];
-        std::memset(&v, 0, sizeof(v));
-        v.n = (uint32_t)M.n[l];
-        v.ld = (uint32_t)M.ld[l];
-        v.nfine = l > 0 ? (uint32_t)M.n[l - 1] : 0u;
-        v.ncoarse = l + 1 < L ? (uint32_t)M.n[l + 1] : 0u;
-        v.nb = M.nb[l];
-        v.ch = M.ch[l];
-        v.agg = M.agg[l];
-        if (l > 0) {
-            conv(M.w[l], 6 * M.ld[l], &v.w);
-            conv(M.dg[l], M.n[l], &v.dg);
-        }
-        conv(M.wd[l], M.n[l] + 1, &v.wd);
-        if (l == 0) {
-            // the CG's own vectors: b = r (one zero entry past the end), out = q
-            v.b = simple ? (f32 ? (T*)H.srf : (T*)H.sr) : (f32 ? (T*)H.arf : (T*)H.ar);
-            v.out = simple ? (f32 ? (T*)H.sqf : (T*)H.sq) : (f32 ? (T*)H.aqf : (T*)H.aq);
-        } else {
-            vec(M.n[l] + 1, &v.b);
-        }
-        vec(M.n[l] + 1, &v.z);
-        vec(M.n[l] + 1, &v.res);
-    }
-    MgLev<T>* dev = nullptr;
-    if (e == cudaSuccess) e = mg_alloc(M, s, &dev, (size_t)L);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dev, d.data(), (size_t)L * sizeof(MgLev<T>), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e == cudaErrorMemoryAllocation)
-        return schur_set_error_internal(SCHUR_ENOMEM, "device allocation failed");
-    if (e != cudaSuccess) return schur_set_error_internal(SCHUR_ECUDA, cudaGetErrorString(e));
-    *out = dev;
-    return SCHUR_OK;
+std::vector<float> to_float(const std::vector<double>& v) {
+    return std::vector<float>(v.begin(), v.end());
 }
 
 int build_hierarchy(Handle& H, MgOp& M, bool simple) {
@@ -620,13 +579,12 @@ int build_hierarchy(Handle& H, MgOp& M, bool simple) {
     std::vector<HostLevel> lv(1);
     if (e == cudaSuccess) e = fine_level(H, simple, lv[0]);
     if (e != cudaSuccess) return schur_set_error_internal(SCHUR_ECUDA, cudaGetErrorString(e));
-    std::vector<std::vector<uint32_t>> aggs, chs(1);
+    std::vector<std::vector<uint32_t>> chs(1);
     do {   // at least one coarse level, until the grid is a single cell
         HostLevel c;
         std::vector<uint32_t> agg, ch;
         if (!coarsen(lv.back(), g.per, ncomp, c, agg, ch))
             return schur_set_error_internal(SCHUR_ECUDA, "multigrid: inconsistent coarse coupling");
-        aggs.push_back(std::move(agg));
         chs.push_back(std::move(ch));
         lv.push_back(std::move(c));
     } while (!single_cell(lv.back()) && (int)lv.size() < kMgMaxLevels);
@@ -637,36 +595,53 @@ int build_hierarchy(Handle& H, MgOp& M, bool simple) {
     const int L = (int)lv.size();
     M.nlev = L;
     M.n.assign(L, 0);
-    M.ld.assign(L, 0);
-    M.nb.assign(L, nullptr);
-    M.ch.assign(L, nullptr);
-    M.agg.assign(L, nullptr);
-    M.w.assign(L, nullptr);
-    M.dg.assign(L, nullptr);
-    M.wd.assign(L, nullptr);
     M.tail = L - 1;
     for (int l = 1; l < L; ++l)
         if (lv[l].n <= kMgTailMax) {
             M.tail = l;
             break;
         }
+    std::vector<MgLev> d((size_t)L);
     for (int l = 0; l < L && e == cudaSuccess; ++l) {
         const HostLevel& v = lv[l];
         M.n[l] = v.n;
-        M.ld[l] = v.ld;
-        if (l + 1 < L) e = upload(M, s, &M.agg[l], aggs[l]);
+        MgLev& dl = d[l];
+        std::memset(&dl, 0, sizeof(dl));
+        dl.n = (uint32_t)v.n;
+        dl.ld = (uint32_t)v.ld;
+        dl.nfine = l > 0 ? (uint32_t)lv[l - 1].n : 0u;
+        dl.fused = v.n <= kMgFuseMax ? 1u : 0u;
         const bool last = (l == L - 1);
-        if (e == cudaSuccess) e = upload(M, s, &M.wd[l], weights(v, last ? 1.0 : kMgOmega));
-        if (l == 0 || e != cudaSuccess) continue;
-        e = upload(M, s, &M.nb[l], v.nb);
-        if (e == cudaSuccess) e = upload(M, s, &M.ch[l], chs[l]);
-        if (e == cudaSuccess) e = upload(M, s, &M.w[l], v.w);
-        if (e == cudaSuccess) e = upload(M, s, &M.dg[l], v.dg);
+        float *wd = nullptr, *w = nullptr, *dg = nullptr;
+        uint32_t *nb = nullptr, *ch = nullptr;
+        e = upload(M, s, &wd, weights(v, last ? 1.0 : kMgOmega));
+        if (e == cudaSuccess && l == 0) e = mg_alloc(M, s, &dl.b, (size_t)v.n + 1);  // FP64 CG: r32
+        if (e == cudaSuccess && l > 0) e = upload(M, s, &nb, v.nb);
+        if (e == cudaSuccess && l > 0) e = upload(M, s, &ch, chs[l]);
+        if (e == cudaSuccess && l > 0) e = upload(M, s, &w, to_float(v.w));
+        if (e == cudaSuccess && l > 0) e = upload(M, s, &dg, to_float(v.dg));
+        if (e == cudaSuccess && l > 0) e = mg_alloc(M, s, &dl.b, (size_t)v.n + 1);
+        if (e == cudaSuccess) e = mg_alloc(M, s, &dl.z, (size_t)v.n + 1);
+        if (e == cudaSuccess) e = mg_alloc(M, s, &dl.res, (size_t)v.n + 1);
+        dl.wd = wd;
+        dl.w = w;
+        dl.dg = dg;
+        dl.nb = nb;
+        dl.ch = ch;
+    }
+    if (e == cudaSuccess) {
+        M.r32 = d[0].b;
+        MgLev* dev = nullptr;
+        e = mg_alloc(M, s, &dev, (size_t)L);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dev, d.data(), (size_t)L * sizeof(MgLev), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        M.lev = dev;
     }
     if (e == cudaErrorMemoryAllocation)
         return schur_set_error_internal(SCHUR_ENOMEM, "device allocation failed");
     if (e != cudaSuccess) return schur_set_error_internal(SCHUR_ECUDA, cudaGetErrorString(e));
-    return build_descriptors<double>(H, M, simple, &M.lev64);
+    return SCHUR_OK;
 }
 
 }  // namespace
@@ -676,24 +651,15 @@ void mg_free(MgOp& M) {
     M = MgOp();
 }
 
-int mg_prepare(Handle& H, bool simple, bool fp32) {
+int mg_prepare(Handle& H, bool simple) {
     MgOp& M = simple ? H.mgS : H.mgA;
-    if ((simple ? H.n_p : H.n_u) == 0) return SCHUR_OK;   // nothing to solve
-    if (!M.nlev) {
-        const long long before = M.bytes;
-        const int rc = build_hierarchy(H, M, simple);
-        if (rc) {
-            mg_free(M);
-            return rc;
-        }
-        H.bytes += M.bytes - before;
+    if ((simple ? H.n_p : H.n_u) == 0 || M.nlev) return SCHUR_OK;
+    const int rc = build_hierarchy(H, M, simple);
+    if (rc) {
+        mg_free(M);
+        return rc;
     }
-    if (fp32 && !M.lev32) {
-        const long long before = M.bytes;
-        const int rc = build_descriptors<float>(H, M, simple, &M.lev32);
-        if (rc) return rc;
-        H.bytes += M.bytes - before;
-    }
+    H.bytes += M.bytes;
     return SCHUR_OK;
 }
 
@@ -703,28 +669,28 @@ void record_mg_loop(Handle& H, Recorder& R, bool simple, bool fp32, void* x, voi
     const Compact C = compact_of(H);
     const long long n = simple ? H.n_p : H.n_u;
     if (!M.nlev) return;   // no entries: the init kernel already finished the solve
+    const MgRun run{(const MgLev*)M.lev, M.nlev, M.tail, (float)(simple ? kMgGammaS : kMgGammaA)};
     if (!fp32) {
-        MgRun<double> run{(const MgLev<double>*)M.lev64, M.nlev, M.tail,
-                          simple ? kMgGammaS : kMgGammaA};
+        // the cycle reads an FP32 copy of the FP64 residual
         if (simple)
             R.launch_coop("mgS_loop", k_mg_loop<double, true>, lgrid(H, n, k_mg_loop<double, true>),
                           sblock(), H.g, C, run, (const double*)H.dSc, (double*)x, (double*)r,
-                          (double*)p, (double*)q, H.dctl, st, H.partials, gate);
+                          (double*)p, (double*)q, M.r32, H.dctl, st, H.partials, gate);
         else
             R.launch_coop("mgA_loop", k_mg_loop<double, false>, lgrid(H, n, k_mg_loop<double, false>),
                           sblock(), H.g, C, run, (const double*)nullptr, (double*)x, (double*)r,
-                          (double*)p, (double*)q, H.dctl, st, H.partials, gate);
+                          (double*)p, (double*)q, M.r32, H.dctl, st, H.partials, gate);
     } else {
-        MgRun<float> run{(const MgLev<float>*)M.lev32, M.nlev, M.tail,
-                         (float)(simple ? kMgGammaS : kMgGammaA)};
+        // FP32 CG: the cycle reads the residual itself (its level-0 descriptor points at r32,
+        // which the kernel does not touch)
         if (simple)
             R.launch_coop("mgS_loop_f32", k_mg_loop<float, true>, lgrid(H, n, k_mg_loop<float, true>),
                           sblock(), H.g, C, run, (const float*)nullptr, (float*)x, (float*)r,
-                          (float*)p, (float*)q, H.dctl, st, H.partials, gate);
+                          (float*)p, (float*)q, (float*)r, H.dctl, st, H.partials, gate);
         else
             R.launch_coop("mgA_loop_f32", k_mg_loop<float, false>, lgrid(H, n, k_mg_loop<float, false>),
                           sblock(), H.g, C, run, (const float*)nullptr, (float*)x, (float*)r,
-                          (float*)p, (float*)q, H.dctl, st, H.partials, gate);
+                          (float*)p, (float*)q, (float*)r, H.dctl, st, H.partials, gate);
     }
 }
 
