@@ -91,95 +91,174 @@ __device__ __forceinline__ float fine_apply(const Tabs<float>& t, const Dev& g, 
     }
 }
 
-// Coarse operator of level L applied at entry i to v.
-__device__ __forceinline__ float coarse_apply(const MgLev& L, uint32_t i, float vi,
-                                              const float* __restrict__ v) {
-    float s = L.dg[i] * vi;
+// Coarse operator of a level (fields of its descriptor) applied at entry i to v.
+__device__ __forceinline__ float coarse_apply(const uint32_t* __restrict__ nb, const float* __restrict__ w,
+                                              const float* __restrict__ dg, uint32_t ld, uint32_t i,
+                                              float vi, const float* __restrict__ v) {
+    float s = dg[i] * vi;
 #pragma unroll
-    for (int e = 0; e < 6; ++e) s += L.w[e * L.ld + i] * v[__ldg(L.nb + e * L.ld + i)];
+    for (int e = 0; e < 6; ++e) s += w[e * ld + i] * v[__ldg(nb + e * ld + i)];
     return s;
 }
 
-// b at entry i of level L: the sum of its children's residuals.
-__device__ __forceinline__ float restrict_at(const MgLev& L, const float* __restrict__ resf, uint32_t i) {
+// b at entry i of a level: the sum of its children's residuals.
+__device__ __forceinline__ float restrict_at(const uint32_t* __restrict__ ch, uint32_t ld,
+                                             const float* __restrict__ resf, uint32_t i) {
     float s = 0.0f;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) s += resf[__ldg(L.ch + c * L.ld + i)];
+    for (int c = 0; c < 8; ++c) s += resf[__ldg(ch + c * ld + i)];
     return s;
 }
 
 // Prolongation of the correction `out` of entry i of level L to its children: y = z + gamma
 // out on the level below F (written into F's res buffer, whose residual is consumed).
-__device__ __forceinline__ void prolong_entry(const MgLev& L, const MgLev& F, float gamma, float out,
-                                              uint32_t i) {
+__device__ __forceinline__ void prolong_entry(const MgLev* __restrict__ L, const MgLev* __restrict__ F,
+                                              float gamma, float out, uint32_t i) {
+    const uint32_t* __restrict__ ch = L->ch;
+    const uint32_t ld = L->ld, nf = L->nfine;
+    const float* __restrict__ zf = F->z;
+    float* __restrict__ yf = F->res;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        const uint32_t k = __ldg(L.ch + c * L.ld + i);
-        if (k < L.nfine) F.res[k] = F.z[k] + gamma * out;
+        const uint32_t k = __ldg(ch + c * ld + i);
+        if (k < nf) yf[k] = zf[k] + gamma * out;
     }
 }
 
-// Fine level, down: res0 = b0 - Op z0.
-template <bool kS>
-__device__ __forceinline__ void mg_down_fine_entry(const Tabs<float>& t, const Dev& g,
-                                                   const Compact& C, const MgLev& L, uint32_t i) {
-    const float* __restrict__ z = L.z;
-    L.res[i] = L.b[i] - fine_apply<kS>(t, g, C, i, z[i], z);
+// Fine-level stencil phase over the whole grid, U entries per thread and step with all of
+// their loads issued before the arithmetic (the gathers are latency-bound).  Down:
+// res0 = b0 - Op z0.  Up: the cycle's output y + wd0 (b0 - Op y), y = res0, handed to
+// emit(i, value).
+template <bool kS, bool kUp, int U, class Emit>
+__device__ __forceinline__ void fine_phase(const Tabs<float>& t, const Dev& g, const Compact& C,
+                                           const MgLev* __restrict__ L, const float* __restrict__ b,
+                                           uint32_t n, Emit emit) {
+    const float* __restrict__ v = kUp ? L->res : L->z;
+    float* __restrict__ res = L->res;
+    const float* __restrict__ wd = L->wd;
+    const int ne = 2 * g.d;
+    const uint32_t* __restrict__ nbt = kS ? C.nbS : C.nbA;
+    const long long ldt = kS ? C.ldS : C.ldA;
+    WARP_STREAM_BEGIN_U(n, U)
+        uint32_t nb[U][6], key[U];
+        float vc[U], bc[U], wc[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j)
+            if (idx[j] < n) {
+#pragma unroll
+                for (int e = 0; e < 6; ++e) nb[j][e] = e < ne ? __ldg(nbt + e * ldt + idx[j]) : n;
+                if constexpr (kS) key[j] = __ldg(C.codeS + idx[j]);
+                else key[j] = C.ufl[idx[j]];
+                vc[j] = v[idx[j]];
+                bc[j] = b[idx[j]];
+                if constexpr (kUp) wc[j] = wd[idx[j]];
+            }
+#pragma unroll
+        for (int j = 0; j < U; ++j)
+            if (idx[j] < n) {
+                float sv[6];
+#pragma unroll
+                for (int e = 0; e < 6; ++e) sv[e] = v[nb[j][e]];
+                float a;
+                if constexpr (!kS) {
+                    a = t.diag[key[j] >> 1] * vc[j] - (((sv[0] + sv[1]) + (sv[2] + sv[3])) + (sv[4] + sv[5]));
+                } else {
+                    a = 0.0f;
+#pragma unroll
+                    for (int e = 0; e < 6; ++e) a += t.w[(key[j] >> (3 * e)) & 7u] * (vc[j] - sv[e]);
+                }
+                if constexpr (kUp) emit(idx[j], vc[j] + wc[j] * (bc[j] - a));
+                else res[idx[j]] = bc[j] - a;
+            }
+    WARP_STREAM_END
 }
 
-// Fine level, up: z = y + wd0 (b0 - Op y), the cycle's output.
-template <bool kS>
-__device__ __forceinline__ float mg_up_fine_entry(const Tabs<float>& t, const Dev& g,
-                                                  const Compact& C, const MgLev& L, uint32_t i) {
-    const float* __restrict__ y = L.res;
-    const float yi = y[i];
-    return yi + L.wd[i] * (L.b[i] - fine_apply<kS>(t, g, C, i, yi, y));
-}
-
-// Coarse level, restriction alone: b = P^T res_(l-1), z = wd b.
-__device__ __forceinline__ void mg_restrict_entry(const MgLev& L, const MgLev& F, uint32_t i) {
-    const float bi = restrict_at(L, F.res, i);
-    L.b[i] = bi;
-    L.z[i] = L.wd[i] * bi;
-}
+// Coarse level, restriction alone over a loop: b = P^T res_(l-1), z = wd b.
+#define MG_RESTRICT(LOOP, Lp, Fp)                                                           \
+    {                                                                                       \
+        const uint32_t* __restrict__ ch_ = (Lp)->ch;                                        \
+        const uint32_t ld_ = (Lp)->ld, n_ = (Lp)->n;                                        \
+        const float* __restrict__ resf_ = (Fp)->res;                                        \
+        const float* __restrict__ wd_ = (Lp)->wd;                                           \
+        float* __restrict__ b_ = (Lp)->b;                                                   \
+        float* __restrict__ z_ = (Lp)->z;                                                   \
+        LOOP(i, n_) {                                                                       \
+            const float bi = restrict_at(ch_, ld_, resf_, i);                               \
+            b_[i] = bi;                                                                     \
+            z_[i] = wd_[i] * bi;                                                            \
+        }                                                                                   \
+    }
 
 // Coarse level, down stencil alone: res = b - A z.
-__device__ __forceinline__ void mg_down_entry(const MgLev& L, uint32_t i) {
-    const float* __restrict__ z = L.z;
-    L.res[i] = L.b[i] - coarse_apply(L, i, z[i], z);
-}
+#define MG_DOWN(LOOP, Lp)                                                                   \
+    {                                                                                       \
+        const uint32_t* __restrict__ nb_ = (Lp)->nb;                                        \
+        const float* __restrict__ w_ = (Lp)->w;                                             \
+        const float* __restrict__ dg_ = (Lp)->dg;                                           \
+        const uint32_t ld_ = (Lp)->ld, n_ = (Lp)->n;                                        \
+        const float* __restrict__ z_ = (Lp)->z;                                             \
+        const float* __restrict__ b_ = (Lp)->b;                                             \
+        float* __restrict__ res_ = (Lp)->res;                                               \
+        LOOP(i, n_) res_[i] = b_[i] - coarse_apply(nb_, w_, dg_, ld_, i, z_[i], z_);        \
+    }
 
 // Coarse level, restriction and down stencil in one phase: b and z are re-formed at the
 // neighbours from their children.
-__device__ __forceinline__ void mg_restrict_down_entry(const MgLev& L, const MgLev& F, uint32_t i) {
-    const float* __restrict__ resf = F.res;
-    const float bi = restrict_at(L, resf, i);
-    const float zi = L.wd[i] * bi;
-    float s = L.dg[i] * zi;
-#pragma unroll
-    for (int e = 0; e < 6; ++e) {
-        const uint32_t j = __ldg(L.nb + e * L.ld + i);
-        s += L.w[e * L.ld + i] * (L.wd[j] * restrict_at(L, resf, j));
+#define MG_RESTRICT_DOWN(LOOP, Lp, Fp)                                                      \
+    {                                                                                       \
+        const uint32_t* __restrict__ nb_ = (Lp)->nb;                                        \
+        const uint32_t* __restrict__ ch_ = (Lp)->ch;                                        \
+        const float* __restrict__ w_ = (Lp)->w;                                             \
+        const float* __restrict__ dg_ = (Lp)->dg;                                           \
+        const float* __restrict__ wd_ = (Lp)->wd;                                           \
+        const uint32_t ld_ = (Lp)->ld, n_ = (Lp)->n;                                        \
+        const float* __restrict__ resf_ = (Fp)->res;                                        \
+        float* __restrict__ b_ = (Lp)->b;                                                   \
+        float* __restrict__ z_ = (Lp)->z;                                                   \
+        float* __restrict__ res_ = (Lp)->res;                                               \
+        LOOP(i, n_) {                                                                       \
+            const float bi = restrict_at(ch_, ld_, resf_, i);                               \
+            const float zi = wd_[i] * bi;                                                   \
+            float s_ = dg_[i] * zi;                                                         \
+            _Pragma("unroll 1") for (int e = 0; e < 6; ++e) {                               \
+                const uint32_t j = __ldg(nb_ + e * ld_ + i);                                \
+                s_ += w_[e * ld_ + i] * (wd_[j] * restrict_at(ch_, ld_, resf_, j));         \
+            }                                                                               \
+            b_[i] = bi;                                                                     \
+            z_[i] = zi;                                                                     \
+            res_[i] = bi - s_;                                                              \
+        }                                                                                   \
     }
-    L.b[i] = bi;
-    L.z[i] = zi;
-    L.res[i] = bi - s;
-}
 
 // Last level: restriction, exact solve z = wd b, prolongation.
-__device__ __forceinline__ void mg_last_entry(const MgLev& L, const MgLev& F, float gamma, uint32_t i) {
-    const float zi = L.wd[i] * restrict_at(L, F.res, i);
-    L.z[i] = zi;
-    prolong_entry(L, F, gamma, zi, i);
-}
+#define MG_LAST(LOOP, Lp, Fp, gamma)                                                        \
+    {                                                                                       \
+        const uint32_t* __restrict__ ch_ = (Lp)->ch;                                        \
+        const uint32_t ld_ = (Lp)->ld, n_ = (Lp)->n;                                        \
+        const float* __restrict__ wd_ = (Lp)->wd;                                           \
+        LOOP(i, n_) {                                                                       \
+            const float zi = wd_[i] * restrict_at(ch_, ld_, (Fp)->res, i);                  \
+            (Lp)->z[i] = zi;                                                                \
+            prolong_entry((Lp), (Fp), (gamma), zi, i);                                      \
+        }                                                                                   \
+    }
 
 // Coarse level, up: out = y + wd (b - A y), prolonged to the level below.
-__device__ __forceinline__ void mg_up_entry(const MgLev& L, const MgLev& F, float gamma, uint32_t i) {
-    const float* __restrict__ y = L.res;
-    const float yi = y[i];
-    const float out = yi + L.wd[i] * (L.b[i] - coarse_apply(L, i, yi, y));
-    prolong_entry(L, F, gamma, out, i);
-}
+#define MG_UP(LOOP, Lp, Fp, gamma)                                                          \
+    {                                                                                       \
+        const uint32_t* __restrict__ nb_ = (Lp)->nb;                                        \
+        const float* __restrict__ w_ = (Lp)->w;                                             \
+        const float* __restrict__ dg_ = (Lp)->dg;                                           \
+        const float* __restrict__ wd_ = (Lp)->wd;                                           \
+        const uint32_t ld_ = (Lp)->ld, n_ = (Lp)->n;                                        \
+        const float* __restrict__ y_ = (Lp)->res;                                           \
+        const float* __restrict__ b_ = (Lp)->b;                                             \
+        LOOP(i, n_) {                                                                       \
+            const float yi = y_[i];                                                         \
+            const float out = yi + wd_[i] * (b_[i] - coarse_apply(nb_, w_, dg_, ld_, i, yi, y_)); \
+            prolong_entry((Lp), (Fp), (gamma), out, i);                                     \
+        }                                                                                   \
+    }
 
 // ---- loops over a level: the whole grid (grid-stride) or block 0 alone -----------------
 
@@ -230,61 +309,56 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
     for (;;) {
         // ---- V-cycle on r (r32 and z0 complete after this barrier)
         if (!(ok = grid_barrier(ctl, target))) break;
-        {
-            MgLev L0 = M.lev[0];
-            L0.b = r32;
-            MG_GRID_LOOP(i, n) mg_down_fine_entry<kS>(tf, g, C, L0, i);
-        }
+        fine_phase<kS, false, 1>(tf, g, C, M.lev, r32, n, [](uint32_t, float) {});
         if (!(ok = grid_barrier(ctl, target))) break;
         for (int l = 1; l < tail; ++l) {
-            const MgLev L = M.lev[l], F = M.lev[l - 1];
-            if (L.fused) {
-                MG_GRID_LOOP(i, L.n) mg_restrict_down_entry(L, F, i);
+            const MgLev* __restrict__ L = M.lev + l;
+            const MgLev* __restrict__ F = M.lev + (l - 1);
+            if (L->fused) {
+                MG_RESTRICT_DOWN(MG_GRID_LOOP, L, F);
             } else {
-                MG_GRID_LOOP(i, L.n) mg_restrict_entry(L, F, i);
+                MG_RESTRICT(MG_GRID_LOOP, L, F);
                 if (!(ok = grid_barrier(ctl, target))) break;
-                MG_GRID_LOOP(i, L.n) mg_down_entry(L, i);
+                MG_DOWN(MG_GRID_LOOP, L);
             }
             if (!(ok = grid_barrier(ctl, target))) break;
         }
         if (!ok) break;
         if (blockIdx.x == 0) {
             for (int l = tail; l < nlev; ++l) {
-                const MgLev L = M.lev[l], F = M.lev[l - 1];
-                if (l == nlev - 1) {
-                    MG_BLOCK_LOOP(i, L.n) mg_last_entry(L, F, gamma, i);
-                } else {
-                    MG_BLOCK_LOOP(i, L.n) mg_restrict_down_entry(L, F, i);
-                }
+                const MgLev* __restrict__ L = M.lev + l;
+                const MgLev* __restrict__ F = M.lev + (l - 1);
+                if (l == nlev - 1) MG_LAST(MG_BLOCK_LOOP, L, F, gamma)
+                else MG_RESTRICT_DOWN(MG_BLOCK_LOOP, L, F)
                 __syncthreads();
             }
             for (int l = nlev - 2; l >= tail; --l) {
-                const MgLev L = M.lev[l], F = M.lev[l - 1];
-                MG_BLOCK_LOOP(i, L.n) mg_up_entry(L, F, gamma, i);
+                const MgLev* __restrict__ L = M.lev + l;
+                const MgLev* __restrict__ F = M.lev + (l - 1);
+                MG_UP(MG_BLOCK_LOOP, L, F, gamma);
                 __syncthreads();
             }
         }
         if (!(ok = grid_barrier(ctl, target))) break;
         for (int l = tail - 1; l >= 1; --l) {
-            {
-                const MgLev L = M.lev[l], F = M.lev[l - 1];
-                MG_GRID_LOOP(i, L.n) mg_up_entry(L, F, gamma, i);
-            }
+            const MgLev* __restrict__ L = M.lev + l;
+            const MgLev* __restrict__ F = M.lev + (l - 1);
+            MG_UP(MG_GRID_LOOP, L, F, gamma);
             if (!(ok = grid_barrier(ctl, target))) break;
         }
         if (!ok) break;
         // ---- z = the cycle's output (into q), r.z and z.z
         double v2[2];
         {
-            MgLev L0 = M.lev[0];
-            L0.b = r32;
             T a0 = (T)0, a1 = (T)0;
-            MG_GRID_LOOP(i, n) {
-                const T zf = (T)mg_up_fine_entry<kS>(tf, g, C, L0, i);
-                qv[i] = zf;
-                a0 += rv[i] * zf;
+            T* __restrict__ q = qv;
+            const T* __restrict__ r = rv;
+            fine_phase<kS, true, 1>(tf, g, C, M.lev, r32, n, [&](uint32_t i, float zf32) {
+                const T zf = (T)zf32;
+                q[i] = zf;
+                a0 += r[i] * zf;
                 a1 += zf * zf;
-            }
+            });
             v2[0] = (double)a0;
             v2[1] = (double)a1;
         }
