@@ -239,12 +239,31 @@ int schur_solve_A(schur_geom_t g, const double* b, double* x, double tol, int ma
  * three for the SIMPLE operator, 6-11 the FP32 versions of 0-5 (after a mixed solve);
  * 12 the persistent inner-A CG kernel that the solver launches (one cooperative launch
  * running SCHUR_TIMED_LOOP_ITERS iterations of all three phases on a fixed right-hand
- * side), 13 the same for the SIMPLE operator, 14-15 their FP32 versions.  Ids 0-11 time
- * the phases one launch each (the solver itself runs them inside 12-15).  The kernel
- * works on the solver's own buffers (their contents after the last call); results of
- * later calls are unaffected.  Synchronises. */
+ * side), 13 the same for the SIMPLE operator, 14-15 their FP32 versions; 16-19 the
+ * multigrid-preconditioned CG kernels (A, SIMPLE, A FP32, SIMPLE FP32; after a solve with
+ * SCHUR_INNER_MG, which builds the hierarchies: SCHUR_ESTATE otherwise), one launch
+ * running SCHUR_TIMED_LOOP_ITERS iterations.  Ids 0-11 time the phases one launch each (the
+ * solver itself runs them inside 12-15).  The kernel works on the solver's own buffers
+ * (their contents after the last call); results of later calls are unaffected.
+ * Synchronises. */
 #define SCHUR_TIMED_LOOP_ITERS 20
 int schur_time_kernel(schur_geom_t g, int kernel, float* ms);
+
+/* Sizes of the multigrid hierarchy of the inner A operator (simple = 0) or of S-hat
+ * (simple = 1), built by the first solve with SCHUR_INNER_MG: *nlev receives the number of
+ * levels (0 when not built), sizes[l] (l < min(nlev, max_levels)) the entries of level l
+ * (level 0: unknown faces or fluid cells), *tail the first level that the loop kernel runs
+ * in one block.  sizes may be NULL. */
+int schur_mg_levels(schur_geom_t g, int simple, int64_t* sizes, int max_levels, int* nlev,
+                    int* tail);
+
+/* Measured FP64 pipe throughput of the current device (no counterpart in the paper: the
+ * roofline denominator of the FP64 kernels).  One launch of a kernel in which every thread
+ * of a grid of (SMs x 8) blocks of 256 threads runs 8 independent chains of `iters`
+ * dependent DFMAs, timed with CUDA events on `stream` after one warm-up launch;
+ * *lane_ops_per_s receives DFMA lane-operations per second (one DFMA = 2 FLOP).  iters in
+ * [1, 1 << 20].  Synchronises `stream`. */
+int schur_fp64_peak(void* stream, int iters, double* lane_ops_per_s);
 
 /* Launch shape of a geometry's kernels: grids are capped at blocks_per_sm (1..32) x SMs
  * (and at the kernel's resident blocks) and give every thread at least
@@ -318,8 +337,10 @@ void schur_batch_destroy(schur_batch_t b);
  * asynchronous solve + recovery, launch shape (8, 1, 0) of schur_set_launch: per-phase
  * graph nodes, so that the jobs in flight interleave), and collects finished ones without
  * blocking; schur_server_take returns finished results.  opts->precond may be
- * SCHUR_PRECOND_AUTO (a per-job choice from the host mask's fluid fraction).  Times are
- * seconds since creation. */
+ * SCHUR_PRECOND_AUTO (a per-job choice from the host mask's fluid fraction).  With
+ * opts->inner_precond = SCHUR_INNER_MG a job's footprint also counts its multigrid
+ * hierarchies (16 bytes per fine entry plus coarse levels of at most a seventh of them) and
+ * its inner solves run as persistent loop kernels.  Times are seconds since creation. */
 typedef struct {
     int64_t id;
     int status;
@@ -332,6 +353,8 @@ typedef struct {
     int pad;
 } schur_job_result;
 
+/* Upper bound of the device memory of one geometry and its solve (Jacobi inner solves;
+ * the server adds the multigrid hierarchies when its solves use them). */
 int64_t schur_footprint_bytes(int ndim, const int64_t dims[3], int precision);
 int schur_server_create(const schur_opts* opts, int64_t mem_budget_bytes, int max_active,
                         schur_server_t* out);

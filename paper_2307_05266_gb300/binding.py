@@ -37,12 +37,13 @@ EXPORTED = [
     "schur_server_submit", "schur_server_progress", "schur_server_take", "schur_server_info",
     "schur_server_destroy",
     "schur_set_launch", "schur_permeability_diag", "schur_history", "schur_cond_estimate",
-    "schur_lanczos_extremes", "schur_set_barrier_limit",
+    "schur_lanczos_extremes", "schur_set_barrier_limit", "schur_fp64_peak", "schur_mg_levels",
 ]
 KERNELS = {"cgA_dir": 0, "cgA_matvec": 1, "cgA_update": 2, "cgS_dir": 3, "cgS_matvec": 4,
            "cgS_update": 5, "cgA_dir_f32": 6, "cgA_matvec_f32": 7, "cgA_update_f32": 8,
            "cgS_dir_f32": 9, "cgS_matvec_f32": 10, "cgS_update_f32": 11,
-           "cgA_loop": 12, "cgS_loop": 13, "cgA_loop_f32": 14, "cgS_loop_f32": 15}
+           "cgA_loop": 12, "cgS_loop": 13, "cgA_loop_f32": 14, "cgS_loop_f32": 15,
+           "mgA_loop": 16, "mgS_loop": 17, "mgA_loop_f32": 18, "mgS_loop_f32": 19}
 # iterations of one timed launch of the persistent loop kernels (ids 12-15)
 TIMED_LOOP_ITERS = 20
 
@@ -117,6 +118,9 @@ def load(build_if_missing: bool = True):
         "schur_time_kernel": (C.c_int, [vp, C.c_int, C.POINTER(C.c_float)]),
         "schur_set_launch": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
         "schur_set_barrier_limit": (C.c_int, [vp, C.c_uint, C.c_int]),
+        "schur_fp64_peak": (C.c_int, [vp, C.c_int, C.POINTER(C.c_double)]),
+        "schur_mg_levels": (C.c_int, [vp, C.c_int, i64p, C.c_int, C.POINTER(C.c_int),
+                                      C.POINTER(C.c_int)]),
         "schur_history": (C.c_int, [vp, C.c_int, vp, vp, vp, vp, C.POINTER(C.c_int)]),
         "schur_cond_estimate": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_double)]),
@@ -353,6 +357,14 @@ class Geometry:
         """Launch shape of this geometry's kernels (see schur_set_launch)."""
         _check(load().schur_set_launch(self._h, blocks_per_sm, entries_per_thread, persistent))
 
+    def mg_levels(self, simple=False):
+        """(entries per level, first one-block level) of the multigrid hierarchy of A or
+        S-hat; ([], 0) before the first multigrid solve (schur_mg_levels)."""
+        sizes = (C.c_int64 * 64)()
+        nlev, tail = C.c_int(), C.c_int()
+        _check(load().schur_mg_levels(self._h, int(simple), sizes, 64, C.byref(nlev), C.byref(tail)))
+        return [int(sizes[i]) for i in range(min(nlev.value, 64))], tail.value
+
     def time_kernel(self, name) -> float:
         """Milliseconds of one launch of a hot kernel (CUDA events on the handle stream)."""
         ms = C.c_float()
@@ -500,3 +512,11 @@ def lanczos_extremes(alpha, beta):
 
 def footprint_bytes(shape, precision=FP64):
     return load().schur_footprint_bytes(len(shape), _dims(shape), precision)
+
+
+def fp64_peak(iters=1 << 16, stream=None):
+    """Measured FP64 DFMA lane-operations per second of the current device
+    (schur_fp64_peak)."""
+    v = C.c_double()
+    _check(load().schur_fp64_peak(C.c_void_p(stream or 0), iters, C.byref(v)))
+    return v.value

@@ -1003,16 +1003,38 @@ int schur_set_barrier_limit(schur_geom_t G, unsigned int polls, int skip_block) 
 
 int schur_time_kernel(schur_geom_t G, int kernel, float* ms) {
     if (!G || !ms) return set_error(SCHUR_EINVAL, "null argument");
-    if (kernel < 0 || kernel > 15) return set_error(SCHUR_EINVAL, "kernel id must be 0..15");
-    if (((kernel > 5 && kernel < 12) || kernel > 13) && !G->H.axf)
+    if (kernel < 0 || kernel > 19) return set_error(SCHUR_EINVAL, "kernel id must be 0..19");
+    if (((kernel > 5 && kernel < 12) || kernel == 14 || kernel == 15 || kernel > 17) && !G->H.axf)
         return set_error(SCHUR_ESTATE, "FP32 kernels need a mixed-precision solve first");
     Handle& H = G->H;
+    if (kernel >= 16 && !((kernel & 1) ? H.mgS.nlev : H.mgA.nlev))
+        return set_error(SCHUR_ESTATE, "multigrid kernels need a solve with SCHUR_INNER_MG first");
     reset_call(H, 0);  // no graph: the condition slot is only written to device memory
     int rc = upload(H);
     if (rc) return rc;
     cudaError_t e = time_kernel(H, kernel, kSlots - 1, ms);
     if (e != cudaSuccess) return cuda_error(e, "time_kernel");
     return download(H);
+}
+
+int schur_mg_levels(schur_geom_t G, int simple, int64_t* sizes, int max_levels, int* nlev,
+                    int* tail) {
+    if (!G || !nlev || !tail || (sizes && max_levels < 0))
+        return set_error(SCHUR_EINVAL, "null or bad argument");
+    const MgOp& M = simple ? G->H.mgS : G->H.mgA;
+    *nlev = M.nlev;
+    *tail = M.tail;
+    if (sizes)
+        for (int l = 0; l < M.nlev && l < max_levels; ++l) sizes[l] = (int64_t)M.n[l];
+    return SCHUR_OK;
+}
+
+int schur_fp64_peak(void* stream, int iters, double* lane_ops_per_s) {
+    if (!lane_ops_per_s) return set_error(SCHUR_EINVAL, "null argument");
+    if (iters < 1 || iters > (1 << 20)) return set_error(SCHUR_EINVAL, "iters must lie in [1, 2^20]");
+    cudaError_t e = measure_fp64_peak((cudaStream_t)stream, iters, lane_ops_per_s);
+    if (e != cudaSuccess) return cuda_error(e, "fp64 peak");
+    return SCHUR_OK;
 }
 
 void schur_destroy(schur_geom_t G) {

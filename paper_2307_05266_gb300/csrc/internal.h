@@ -139,6 +139,7 @@ void record_recover(Handle& H, Recorder& R);
 void record_solve_recover(Handle& H, Recorder& R, int precond, int precision);
 void record_solve_A(Handle& H, Recorder& R, const double* b, double* x);
 cudaError_t time_kernel(Handle& H, int which, int slot, float* ms);
+cudaError_t measure_fp64_peak(cudaStream_t s, int iters, double* lane_ops_per_s);
 
 // mg.cu: build the multigrid hierarchy of A (simple = false) or S-hat (simple = true) when
 // missing (returns a SCHUR_* code); record the

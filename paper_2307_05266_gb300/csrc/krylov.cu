@@ -1136,7 +1136,8 @@ __global__ void k_fill_pattern(double* __restrict__ v, long long n) {
 // SCHUR_TIMED_LOOP_ITERS iterations (tolerance 0) from a fixed right-hand side: the A loop
 // from b = f, the SIMPLE loop from a hashed cell vector.  Only the loop launch is timed.
 template <typename T>
-static cudaError_t time_loop_t(Handle& H, bool simple, InnerA<T> a, InnerS<T> sv, float* ms) {
+static cudaError_t time_loop_t(Handle& H, bool simple, InnerA<T> a, InnerS<T> sv, float* ms,
+                               bool mg = false) {
     Ctl* ctl = H.dctl;
     CgState* st = &ctl->solo;
     const Compact C = compact_of(H);
@@ -1157,7 +1158,15 @@ static cudaError_t time_loop_t(Handle& H, bool simple, InnerA<T> a, InnerS<T> sv
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaEventRecord(H.ev0, H.stream)) != cudaSuccess) return e;
-    if (!simple) {
+    if (mg) {
+        int slot = kSlots - 1;
+        Recorder R(H.stream, ctl, &slot);
+        if (!simple)
+            record_mg_loop(H, R, false, sizeof(T) == sizeof(float), a.x, a.r, a.p, a.q, st, nullptr);
+        else
+            record_mg_loop(H, R, true, sizeof(T) == sizeof(float), sv.x, sv.r, sv.p, sv.q, st, nullptr);
+        if (!R.ok()) return R.error();
+    } else if (!simple) {
         void* args[] = {(void*)&H.g, (void*)&C, (void*)&a.x, (void*)&a.r, (void*)&a.p, (void*)&a.q,
                         (void*)&ctl, (void*)&st, (void*)&H.partials};
         e = cudaLaunchCooperativeKernel((const void*)k_cgA_loop<T>, lgrid(H, H.n_u, k_cgA_loop<T>), b,
@@ -1182,6 +1191,10 @@ static cudaError_t time_loop(Handle& H, int which, float* ms) {
         case 13: return time_loop_t<double>(H, true, innerA64(H), innerS64(H), ms);
         case 14: return time_loop_t<float>(H, false, innerA32(H), innerS32(H), ms);
         case 15: return time_loop_t<float>(H, true, innerA32(H), innerS32(H), ms);
+        case 16: return time_loop_t<double>(H, false, innerA64(H), innerS64(H), ms, true);
+        case 17: return time_loop_t<double>(H, true, innerA64(H), innerS64(H), ms, true);
+        case 18: return time_loop_t<float>(H, false, innerA32(H), innerS32(H), ms, true);
+        case 19: return time_loop_t<float>(H, true, innerA32(H), innerS32(H), ms, true);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1192,7 +1205,8 @@ cudaError_t time_kernel(Handle& H, int which, int slot, float* ms) {
         if (e == cudaSuccess) e = cudaEventCreate(&H.ev1);
         if (e != cudaSuccess) return e;
     }
-    if (((which >= 6 && which < 12) || which >= 14) && !H.axf) return cudaErrorInvalidValue;
+    if (((which >= 6 && which < 12) || which == 14 || which == 15 || which >= 18) && !H.axf)
+        return cudaErrorInvalidValue;
     Ctl* ctl = H.dctl;
     CgState* st = &ctl->solo;
     const long long nu = H.n_u, np = H.n_p;
@@ -1225,6 +1239,53 @@ cudaError_t time_kernel(Handle& H, int which, int slot, float* ms) {
     if (e == cudaSuccess) e = cudaEventRecord(H.ev1, H.stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(H.ev1);
     if (e == cudaSuccess) e = cudaEventElapsedTime(ms, H.ev0, H.ev1);
+    return e;
+}
+
+// FP64 pipe throughput: 8 independent chains of dependent DFMAs per thread (the chains
+// keep the pipe busy; the result is stored so that nothing is optimised away).
+__global__ void k_dfma_peak(double* __restrict__ out, int iters, double x, double y) {
+    double a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = (double)(threadIdx.x + k) * 1e-3;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fma(a[k], x, y);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+cudaError_t measure_fp64_peak(cudaStream_t s, int iters, double* lane_ops_per_s) {
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int blocks = nsm * 8, threads = 256;
+    double* out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaMalloc((void**)&out, (size_t)blocks * threads * sizeof(double));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) {
+        // x slightly below 1 and y small keep every chain bounded and normal
+        k_dfma_peak<<<blocks, threads, 0, s>>>(out, iters, 0.999999, 1e-6);   // warm-up
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        k_dfma_peak<<<blocks, threads, 0, s>>>(out, iters, 0.999999, 1e-6);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (out) cudaFree(out);
+    if (e == cudaSuccess)
+        *lane_ops_per_s = (double)blocks * threads * 8.0 * (double)iters / ((double)ms * 1e-3);
     return e;
 }
 

@@ -311,6 +311,13 @@ extern "C" int schur_server_submit(schur_server_t s, const uint8_t* host_mask, i
         j.precond = (double)fluid < SCHUR_AUTO_SIMPLE_BELOW * (double)nc ? SCHUR_SIMPLE : SCHUR_UZAWA;
     }
     j.bytes = schur_footprint_bytes(ndim, j.dims, s->opts.precision);
+    if (s->opts.inner_precond == SCHUR_INNER_MG) {
+        // multigrid hierarchies: per fine entry 16 bytes (weights, work vectors, FP32
+        // residual), and coarse levels of at most 1/7 of the fine entries at ~104 bytes
+        const int64_t nc = j.dims[0] * j.dims[1] * (ndim == 3 ? j.dims[2] : 1);
+        const int64_t nf = (int64_t)ndim * nc;
+        j.bytes += 16 * (nf + nc) + 104 * (nf + nc) / 7 + (1 << 20);
+    }
     if (j.bytes > s->budget) return schur_set_error_internal(SCHUR_ENOMEM, "job larger than the memory budget");
     j.t_submit = now_s(s);
     if (job_id) *job_id = j.id;
