@@ -1,10 +1,11 @@
 """Benchmark of the GB300 Schur-complement Stokes path.
 
 Headline step = create_geometry (mask -> face flags, components, work lists) followed,
-for Uzawa and for SIMPLE, by schur_solve (Algorithm 1 to tol 1e-8, inner tolerances
-1e-12, FP64), velocity recovery and the permeability read-back: two Schur solves per step
-on "spheres128" (128^3 periodic overlapping spheres, radii U[4,8), porosity 0.40, seed 0,
-f = e_x).
+for Uzawa and for SIMPLE, by schur_solve (Algorithm 1 to tol 1e-8, FP64, inner CG to
+1e-12 preconditioned by the aggregation-multigrid V-cycle), velocity recovery and the
+permeability read-back: two Schur solves per step on "spheres128" (128^3 periodic
+overlapping spheres, radii U[4,8), porosity 0.40, seed 0, f = e_x).  The same step with
+Jacobi inner solves is timed once after the timed region and reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--patterns mixed,batch,serve,tight,suite2d|none]
@@ -40,7 +41,8 @@ WORKLOAD = dict(name="spheres128", n=128, r_min=4.0, r_max=8.0, porosity=0.40, s
                 force=(1.0, 0.0, 0.0), tol=1e-8, tol_inner=1e-12)
 DESC = ("spheres128: 128^3 periodic overlapping solid spheres, radii U[4,8), porosity "
         "0.40, seed 0 (+rank), f = e_x, FP64; Uzawa and SIMPLE Schur-CG to 1e-8 "
-        "(unpreconditioned), inner Jacobi-PCG to 1e-12")
+        "(unpreconditioned), inner CG to 1e-12 preconditioned by the aggregation-multigrid "
+        "V-cycle (FP32 cycle)")
 
 
 # Per hot kernel and entry (unknown face for cgA_*, fluid cell for cgS_*): algorithmic
@@ -56,9 +58,36 @@ DESC = ("spheres128: 128^3 periodic overlapping solid spheres, radii U[4,8), por
 #   cgS_update  x, r, r.z, z.z                read x, p, r, q, invd; write x, r 5 ops
 #   cgA_loop / cgS_loop  the persistent kernel the solver launches: one launch runs
 #               binding.TIMED_LOOP_ITERS iterations of the three phases above (timed case)
-def kernel_model(name, nu, npf, d, loop_iters=20):
+# Multigrid-preconditioned CG, one iteration (mgA_loop / mgS_loop; FP32 V-cycle, CG in w),
+# per fine entry, t = 2d * 4 table bytes, f = flag byte (A) or 4-byte face code (S):
+#   x/r update, FP32 residual, z0      read x, p, r, q, wd0; write x, r, (r32,) z0
+#   fine down stencil res0 = r - A z0  read table, f, z0, r32; write res0
+#   fine up stencil z = y + wd0 (...)  read table, f, res0 (= y), r32, wd0, r; write q
+#   direction p = z + beta p           read q, p; write p
+#   matvec q = A p, p.q                read table, f, p (, dS); write q
+# and per coarse entry (FP32): the fused restriction + down stencil reads the children
+# table (32), the 7-point table and coefficients (24 + 24 + 4 + 4), the children's
+# residuals (32) and writes b, z, res (12); the up stencil reads the 7-point table and
+# coefficients, y, b, the children table and the children's z (56 + 8 + 32 + 32) and
+# writes the children's y (32).  FP64 lane-operations: the CG part only (the cycle is FP32).
+def mg_model(simple, n0, coarse, d, w):
+    t = 2 * d * 4
+    f = 4 if simple else 1
+    fine = (6 * w + 4 + (4 if w == 8 else 0) + 4) + (t + f + 8 + 4) + (t + f + 12 + w + w) \
+        + 3 * w + (t + f + w + w + (w if (simple and w == 8) else 0))
+    coarse_b = sum(coarse) * ((32 + 56 + 32 + 12) + (56 + 8 + 32 + 32 + 32))
+    ops = (2 + 2 + 1 + (8 if simple else 7) + 1) * n0 if w == 8 else 0
+    return fine * n0 + coarse_b, ops
+
+
+def kernel_model(name, nu, npf, d, loop_iters=20, mg=None):
     w = 4 if name.endswith("_f32") else 8
     base = name.replace("_f32", "")
+    if base in ("mgA_loop", "mgS_loop"):
+        simple = base == "mgS_loop"
+        sizes = (mg or {}).get("S" if simple else "A") or [npf if simple else nu]
+        b, ops = mg_model(simple, sizes[0], sizes[1:], d, w)
+        return loop_iters * b, loop_iters * ops, w
     if base in ("cgA_loop", "cgS_loop"):
         suf = "_f32" if name.endswith("_f32") else ""
         ph = ("cgA_dir", "cgA_matvec", "cgA_update") if base == "cgA_loop" else \
@@ -93,7 +122,8 @@ NCU_TRAFFIC = {
 def kernel_sources_sha():
     import hashlib
     h = hashlib.sha256()
-    for rel in ("paper_2307_05266_gb300/csrc/krylov.cu", "paper_2307_05266_gb300/csrc/common.cuh"):
+    for rel in ("paper_2307_05266_gb300/csrc/krylov.cu", "paper_2307_05266_gb300/csrc/common.cuh",
+                "paper_2307_05266_gb300/csrc/cg_dev.cuh", "paper_2307_05266_gb300/csrc/mg.cu"):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -210,7 +240,7 @@ def reference_arm(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": DESC, "parallelism": "replicas"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample_text(s)},
+                         "sample": sample_text(s), "nproc": os.cpu_count(), "extrapolated": True},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -322,18 +352,21 @@ def job_rate(ms_local, units_per_rank, world, device):
     return units_per_rank * world / (ms_max / 1e3), ms_max
 
 
-def time_kernels(binding, torch, mask_dev, reps):
-    """Per-kernel timing on the headline workload: CUDA events around single launches on
-    the geometry's stream, L2 flushed before every launch by reading a 512 MiB buffer
-    (clean lines, so the timed kernel pays no write-back of the flush), mean over reps - 2
-    launches; the FP32 kernels run on the buffers of a mixed-precision solve."""
+def time_kernels(binding, torch, mask_dev, reps, names=None):
+    """Per-kernel timing on a workload: CUDA events around single launches on the
+    geometry's stream, L2 flushed before every launch by reading a 512 MiB buffer (clean
+    lines, so the timed kernel pays no write-back of the flush), mean over reps - 2 launches;
+    the FP32 kernels run on the buffers of a mixed-precision solve and the multigrid kernels
+    on the hierarchies it builds.  Roofline denominators: the measured HBM copy bandwidth
+    (MEASURED_PEAKS.json) and the FP64 DFMA throughput measured by schur_fp64_peak."""
     w = WORKLOAD
     peak_bw, sm_mhz, _ = load_peaks()
-    nsm = torch.cuda.get_device_properties(0).multi_processor_count
-    fp64_peak = nsm * 2 * sm_mhz * 1e6 / 1e12
+    fp64_peak = binding.fp64_peak() / 1e12
     g = binding.Geometry(mask_dev)
     g.set_force(w["force"])
-    g.solve(precond=binding.SIMPLE, precision=binding.MIXED, tol=w["tol"])
+    g.solve(precond=binding.SIMPLE, precision=binding.MIXED, tol=w["tol"],
+            inner_precond=binding.INNER_MG)
+    mg = {"A": g.mg_levels(False)[0], "S": g.mg_levels(True)[0]}
     info = g.info
     nu = int(sum(info.n_unknown[a] for a in range(info.ndim)))
     npf = int(info.n_fluid)
@@ -341,13 +374,13 @@ def time_kernels(binding, torch, mask_dev, reps):
     sink = torch.empty((), dtype=torch.float64, device="cuda")
     traffic_ok = NCU_TRAFFIC["sources_sha256"] == kernel_sources_sha()
     kern = {}
-    for name in binding.KERNELS:
+    for name in names or binding.KERNELS:
         times = []
         for _ in range(reps):
             torch.sum(flush, 0, out=sink)
             times.append(g.time_kernel(name))
         avg = statistics.mean(times[2:]) if reps > 2 else statistics.mean(times)
-        b, ops, wb = kernel_model(name, nu, npf, info.ndim, binding.TIMED_LOOP_ITERS)
+        b, ops, wb = kernel_model(name, nu, npf, info.ndim, binding.TIMED_LOOP_ITERS, mg)
         gbps = b / (avg / 1e3) / 1e9
         tops = ops / (avg / 1e3) / 1e12
         f_hbm, f_alu = gbps / peak_bw, (tops / fp64_peak if wb == 8 else 0.0)
@@ -357,10 +390,11 @@ def time_kernels(binding, torch, mask_dev, reps):
                       "fp64_lane_ops": ops if wb == 8 else 0,
                       "fp64_Tops": tops if wb == 8 else 0.0, "frac_hbm": f_hbm,
                       "frac_fp64_pipe": f_alu, "ncu_dram_bytes": tr,
+                      "l2_resident": (tr is not None and tr < 0.5 * b),
                       "bound": "alu" if f_alu > f_hbm else "hbm"}
     g.close()
     del flush
-    return kern, nu, npf
+    return kern, nu, npf, mg, fp64_peak
 
 
 def kernels_only(args):
@@ -372,8 +406,9 @@ def kernels_only(args):
     torch.cuda.set_device(0)
     binding.load()
     mask_dev = torch.from_numpy(make_mask(0)).cuda()
-    kern, nu, npf = time_kernels(binding, torch, mask_dev, max(1, args.steps))
-    print(json.dumps({"workload": DESC, "n_unknown": nu, "n_fluid": npf, "kernels": kern}))
+    kern, nu, npf, mg, _ = time_kernels(binding, torch, mask_dev, max(1, args.steps))
+    print(json.dumps({"workload": DESC, "n_unknown": nu, "n_fluid": npf, "mg_levels": mg,
+                      "kernels": kern}))
     return 0
 
 
@@ -417,8 +452,10 @@ def gpu_arm(args):
     porosity = float(mask_np.mean())
     stream = torch.cuda.current_stream()
     precs = (("uzawa", binding.UZAWA), ("simple", binding.SIMPLE))
+    inner = binding.INNER_MG if args.inner == "mg" else binding.INNER_JACOBI
     solve_kw = dict(tol=w["tol"], tol_inner_A=w["tol_inner"], tol_inner_S=w["tol_inner"],
-                    loop_mode=binding.LOOP_HOST if args.loop == "host" else binding.LOOP_GRAPH)
+                    loop_mode=binding.LOOP_HOST if args.loop == "host" else binding.LOOP_GRAPH,
+                    inner_precond=inner)
 
     def step(mask, rec):
         g = binding.Geometry(mask)
@@ -479,15 +516,13 @@ def gpu_arm(args):
 
     peak_bw, sm_mhz, peak_kind = load_peaks()
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
-    fp64_peak = nsm * 2 * sm_mhz * 1e6 / 1e12   # T lane-ops/s: 2 FP64 lanes per clock and SM
-    kern, nu, npf = time_kernels(binding, torch, mask_dev, 12)
-    # time share of each FP64 kernel in one headline step (launch counts from iterations)
+    kern, nu, npf, mg_levels, fp64_peak = time_kernels(binding, torch, mask_dev, 12)
+    # time share of each inner-solve kernel in one headline step (iterations x the time of
+    # one iteration; the timed launch of a loop kernel covers TIMED_LOOP_ITERS iterations)
     launches_of = {"A": sum(per[p]["inner_A"] + per[p]["recovery"] for p in per),
                    "S": sum(per[p]["inner_S"] for p in per)}
-    # (the solver runs the persistent loop kernels; their timed launch covers
-    # TIMED_LOOP_ITERS iterations)
-    share = {k: kern[k]["ms"] / binding.TIMED_LOOP_ITERS * launches_of[k[2]]
-             for k in ("cgA_loop", "cgS_loop")}
+    loops = ("mgA_loop", "mgS_loop") if args.inner == "mg" else ("cgA_loop", "cgS_loop")
+    share = {k: kern[k]["ms"] / binding.TIMED_LOOP_ITERS * launches_of[k[2]] for k in loops}
     tot = sum(share.values())
     for k in share:
         kern[k]["step_share"] = share[k] / tot
@@ -499,11 +534,13 @@ def gpu_arm(args):
             return {"bound": "alu", "kernel": name, "achieved": kk["fp64_Tops"],
                     "peak": fp64_peak, "unit": "T FP64 lane-ops/s", "frac": kk["frac_fp64_pipe"],
                     "traffic": kk["ncu_dram_bytes"], "alg_bytes": kk["alg_bytes"],
-                    "peak_kind": f"derived FP64 pipe peak: {nsm} SMs x 2 lanes/clk x "
-                                 f"{sm_mhz:.0f} MHz (DFMA, DADD, DMUL one lane-op each)"}
+                    "frac_hbm": kk["frac_hbm"],
+                    "peak_kind": "measured FP64 DFMA throughput (schur_fp64_peak; nominal "
+                                 f"{nsm} SMs x 2 lanes/clk x {sm_mhz:.0f} MHz = "
+                                 f"{nsm * 2 * sm_mhz * 1e6 / 1e12:.3f})"}
         return {"bound": "hbm", "kernel": name, "achieved": kk["alg_GBps"], "peak": peak_bw,
                 "unit": "GB/s", "frac": kk["frac_hbm"], "traffic": kk["ncu_dram_bytes"],
-                "alg_bytes": kk["alg_bytes"],
+                "alg_bytes": kk["alg_bytes"], "frac_fp64_pipe": kk["frac_fp64_pipe"],
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)"}
 
     roof = roof_of(dom)
@@ -511,6 +548,7 @@ def gpu_arm(args):
                       "timed region, L2 flushed before each launch, mean of 10; a launch of the "
                       "persistent loop kernel runs %d CG iterations; dominant kernel = largest "
                       "time share of the headline step" % binding.TIMED_LOOP_ITERS)
+    roof["fp64_peak_measured_Tops"] = fp64_peak
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -524,9 +562,11 @@ def gpu_arm(args):
                          f"{info.device_bytes / 1e9:.2f} GB vs 0.13 GB L2",
                    "parallelism": f"replicas x{world}"},
         "per_precond": per,
+        "inner_precond": args.inner,
+        "mg_levels": mg_levels,
         "kernels": kern,
         "roofline": roof,
-        "roofline_mixed": roof_of(max(("cgA_loop_f32", "cgS_loop_f32"),
+        "roofline_mixed": roof_of(max(tuple(k + "_f32" for k in loops),
                                       key=lambda k: kern[k]["ms"] / binding.TIMED_LOOP_ITERS
                                       * launches_of[k[2]])),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(mask_np.nbytes),
@@ -535,6 +575,8 @@ def gpu_arm(args):
         "clocks": clk.summary(),
     }
 
+    if world == 1 and "jacobi" in patterns:
+        line["inner_jacobi"] = jacobi_pattern(binding, torch, mask_dev, per, solve_kw, args)
     if world == 1 and "mixed" in patterns:
         line["mixed_precision"] = mixed_pattern(binding, mask_dev, per, solve_kw)
     if world == 1 and "suite2d" in patterns:
@@ -555,7 +597,12 @@ def gpu_arm(args):
     cpu = run_oracle_subprocess(1) if world == 1 else None
     if cpu is not None and cpu.get("ok"):
         line["cpu_baseline"] = {"value": cpu["value"], "unit": UNIT, "cores": 1,
-                                "kind": "oracle", "sample": sample_text(cpu)}
+                                "kind": "oracle", "sample": sample_text(cpu),
+                                "nproc": os.cpu_count(), "extrapolated": True,
+                                "sampled_iterations": {"inner_A": 12, "inner_S": 10},
+                                "note": "SciPy's CSR products run on one thread whatever the "
+                                        "thread settings, so the oracle uses one of the "
+                                        "host's cores"}
     elif cpu is not None:
         line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": cpu.get("why", "unavailable")}
@@ -563,6 +610,31 @@ def gpu_arm(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def jacobi_pattern(binding, torch, mask_dev, per, solve_kw, args):
+    """The headline step's solves with the other inner preconditioner (Jacobi when the
+    headline runs the multigrid), one timed run each after a warm-up, FP64."""
+    other = "jacobi" if args.inner == "mg" else "mg"
+    kw = dict(solve_kw, inner_precond=binding.INNER_JACOBI if other == "jacobi" else binding.INNER_MG)
+    out = {"inner_precond": other}
+    g = binding.Geometry(mask_dev)
+    g.set_force(WORKLOAD["force"])
+    for name, pc in (("uzawa", binding.UZAWA), ("simple", binding.SIMPLE)):
+        g.solve(precond=pc, **kw)
+        g.recover_velocity()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = g.solve(precond=pc, **kw)
+        rs = g.recover_velocity()
+        k = g.permeability(0)
+        dt = (time.perf_counter() - t0) * 1e3
+        out[name] = {"ms": dt, "outer": st.outer_iters, "inner_A": st.inner_iters_A,
+                     "inner_S": st.inner_iters_S, "recovery": rs.inner_iters_A, "k": k,
+                     "k_rel_diff": abs(k - per[name]["k"]) / abs(per[name]["k"]),
+                     "headline_speedup": dt / per[name]["ms_median"]}
+    g.close()
+    return out
 
 
 def mixed_pattern(binding, mask_dev, per, solve_kw):
@@ -576,7 +648,7 @@ def mixed_pattern(binding, mask_dev, per, solve_kw):
         for i in range(3):
             t0 = time.perf_counter()
             st = g.solve(precond=pc, precision=binding.MIXED, tol=WORKLOAD["tol"],
-                         tol_inner_A=WORKLOAD["tol_inner"])
+                         tol_inner_A=WORKLOAD["tol_inner"], inner_precond=solve_kw["inner_precond"])
             g.recover_velocity()
             k = g.permeability(0)
             if i:
@@ -618,11 +690,25 @@ def batch_pattern(binding, torch, masks, stream):
         g.solve(**opts)
         g.recover_velocity()
     t_seq = time.perf_counter() - t0
+    # the plain FP64 path on the same 64 inputs (same preconditioner choice, multigrid
+    # inner solves as in the headline), one after another
+    kw64 = dict(precond=binding.PRECOND_AUTO, tol=1e-8, inner_precond=binding.INNER_MG)
+    geoms[0].solve(**kw64)                              # warm-up (graph recording)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for g in geoms[:8]:
-        g.solve(precond=binding.UZAWA, tol=1e-8)
+    for g in geoms:
+        g.solve(**kw64)
         g.recover_velocity()
-    t_seq64 = (time.perf_counter() - t0) / 8
+    t_seq64 = time.perf_counter() - t0
+    # the batch with multigrid inner solves (persistent loop kernels, 2 blocks per SM each)
+    kwmg = dict(opts, inner_precond=binding.INNER_MG)
+    bm = binding.Batch(geoms, blocks_per_sm=2, **kwmg)
+    bm.run()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ssm, _, _ = bm.run()
+    t_batch_mg = time.perf_counter() - t0
+    bm.close()
     cells = [m.size for m in masks]
     for g in geoms:
         g.close()
@@ -634,9 +720,11 @@ def batch_pattern(binding, torch, masks, stream):
                                 "persistent_inner": best[2]}, "batch_s": t_batch,
             "batch_solves_per_s": len(masks) / t_batch,
             "sequential_mixed_solves_per_s": len(masks) / t_seq,
-            "sequential_fp64_solves_per_s_first8": 1.0 / t_seq64,
+            "sequential_fp64_mg_solves_per_s": len(masks) / t_seq64,
             "speedup_batch_vs_sequential_mixed": t_seq / t_batch,
-            "all_converged": all(s.status == 0 for s in ss)}
+            "speedup_batch_vs_sequential_fp64": t_seq64 / t_batch,
+            "batch_mg_solves_per_s": len(masks) / t_batch_mg,
+            "all_converged": all(s.status == 0 for s in ss) and all(s.status == 0 for s in ssm)}
 
 
 def serve_pattern(binding, torch, masks, axes, rng, args):
@@ -645,10 +733,11 @@ def serve_pattern(binding, torch, masks, axes, rng, args):
     budget = int(0.6 * free)
     # per-request preconditioner: SIMPLE below 0.25 porosity, where Uzawa needs thousands of
     # outer iterations (the stagnation of Section 4 that motivates SIMPLE), Uzawa otherwise
-    opts = dict(precond=binding.PRECOND_AUTO, precision=binding.MIXED, tol=1e-8, max_outer=20000)
+    opts = dict(precond=binding.PRECOND_AUTO, precision=binding.MIXED, tol=1e-8, max_outer=20000,
+                inner_precond=binding.INNER_MG)
 
-    def run(arrivals, max_active):
-        srv = binding.Server(budget, max_active=max_active, **opts)
+    def run(arrivals, max_active, **over):
+        srv = binding.Server(budget, max_active=max_active, **dict(opts, **over))
         t0 = time.perf_counter()
         sub = 0
         res = {}
@@ -675,8 +764,13 @@ def serve_pattern(binding, torch, masks, axes, rng, args):
         arrivals.append(t)
     res, wall, info = run(arrivals, 16)
     lat = [r["t_done"] - r["t_submit"] for r in res]
+    # the plain FP64 path on the same requests and arrival times
+    res64, wall64, info64 = run(arrivals, 16, precision=binding.FP64)
+    lat64 = [r["t_done"] - r["t_submit"] for r in res64]
+    k_diff = [abs(a["k"] - b["k"]) / max(abs(b["k"]), 1e-300) for a, b in zip(res, res64)]
     return {"requests": len(masks), "edges": [int(round(m.size ** (1 / 3))) for m in masks],
             "precond": "auto: simple below porosity %.2f, else uzawa" % binding.AUTO_SIMPLE_BELOW,
+            "inner_precond": "mg",
             "precision": "mixed", "arrival_rate_per_s": rate,
             "preconds": ["simple" if r["precond"] == binding.SIMPLE else "uzawa" for r in res],
             "capacity_per_s": capacity, "p50_s": pct(lat, 0.5), "p99_s": pct(lat, 0.99),
@@ -684,7 +778,12 @@ def serve_pattern(binding, torch, masks, axes, rng, args):
             "peak_active": info["peak_active"], "peak_bytes": info["peak_bytes"],
             "budget_bytes": budget, "all_ok": all(r["status"] == 0 for r in res),
             "status": [r["status"] for r in res], "outer_iters": [r["outer_iters"] for r in res],
-            "latency_s": lat}
+            "latency_s": lat,
+            "fp64_same_stream": {"p50_s": pct(lat64, 0.5), "p99_s": pct(lat64, 0.99),
+                                 "solves_per_s": len(res64) / max(r["t_done"] for r in res64),
+                                 "all_ok": all(r["status"] == 0 for r in res64),
+                                 "peak_active": info64["peak_active"], "latency_s": lat64,
+                                 "k_rel_diff_mixed_vs_fp64_max": max(k_diff)}}
 
 
 # Tight geometry: 256^3, porosity 0.15, radii U[2, 4) (high surface-to-volume ratio).
@@ -702,13 +801,16 @@ def tight_pattern(binding, torch, mask):
     info = g.info
     out["n_unknown"] = int(sum(info.n_unknown[a] for a in range(info.ndim)))
     out["n_fluid"] = int(info.n_fluid)
-    runs = (("fp64_simple", binding.SIMPLE, binding.FP64),
-            ("mixed_simple", binding.SIMPLE, binding.MIXED),
-            ("mixed_uzawa", binding.UZAWA, binding.MIXED))
-    for name, pc, prec in runs:
+    MG, JAC = binding.INNER_MG, binding.INNER_JACOBI
+    runs = (("fp64_simple", binding.SIMPLE, binding.FP64, MG),
+            ("mixed_simple", binding.SIMPLE, binding.MIXED, MG),
+            ("mixed_uzawa", binding.UZAWA, binding.MIXED, MG),
+            ("mixed_simple_jacobi", binding.SIMPLE, binding.MIXED, JAC))
+    for name, pc, prec, inner in runs:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st = g.solve(precond=pc, precision=prec, tol=1e-8, max_outer=20000, allow_fail=True)
+        st = g.solve(precond=pc, precision=prec, tol=1e-8, max_outer=20000, allow_fail=True,
+                     inner_precond=inner)
         g.recover_velocity(allow_fail=True)
         k = g.permeability(0)
         dt = time.perf_counter() - t0
@@ -717,8 +819,14 @@ def tight_pattern(binding, torch, mask):
                      "inner_A_f32": st.inner_iters_A_f32, "inner_S_f32": st.inner_iters_S_f32,
                      "refinements": st.refinements, "k": k}
     g.close()
+    # loop kernels in the HBM regime: the FP64 A working set (~0.3 GB) exceeds the L2
+    kern, _, _, mg, _ = time_kernels(binding, torch, torch.from_numpy(mask).cuda(), 6,
+                                     names=["cgA_loop", "cgS_loop", "cgA_loop_f32", "cgS_loop_f32",
+                                            "mgA_loop", "mgS_loop", "mgA_loop_f32", "mgS_loop_f32"])
+    out["kernels"] = kern
+    out["mg_levels"] = mg
     k64 = out["fp64_simple"]["k"]
-    for name in ("mixed_simple", "mixed_uzawa"):
+    for name in ("mixed_simple", "mixed_uzawa", "mixed_simple_jacobi"):
         out[name]["k_rel_err_vs_gpu_fp64"] = abs(out[name]["k"] - k64) / abs(k64)
         out[name]["speedup_vs_fp64_simple"] = out["fp64_simple"]["s"] / out[name]["s"]
     return out
@@ -780,9 +888,11 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--patterns", default="mixed,batch,serve,tight,suite2d")
-    ap.add_argument("--serve-requests", type=int, default=16)
-    ap.add_argument("--serve-max-edge", type=int, default=192)
+    ap.add_argument("--patterns", default="jacobi,mixed,batch,serve,tight,suite2d")
+    ap.add_argument("--inner", default="mg", choices=["mg", "jacobi"],
+                    help="inner preconditioner of the headline step")
+    ap.add_argument("--serve-requests", type=int, default=8)
+    ap.add_argument("--serve-max-edge", type=int, default=384)
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="host: loops driven from the host, one plain launch per kernel (for "
                          "profilers that cannot see kernel nodes under conditional nodes)")
