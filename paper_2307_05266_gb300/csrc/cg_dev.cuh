@@ -376,17 +376,17 @@ static inline dim3 tgrid(const Handle& H) {
     return dim3((unsigned)(nt < H.target_blocks ? nt : H.target_blocks));
 }
 // Resident blocks of kBlock threads per SM for kernel k (cached per device and kernel).
-static int resident_blocks(const void* k) {
+static int resident_blocks(const void* k, size_t smem = 0) {
     static std::mutex mu;
-    static std::map<std::pair<int, const void*>, int> cache;
+    static std::map<std::pair<std::pair<int, const void*>, size_t>, int> cache;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
     std::lock_guard<std::mutex> lock(mu);
-    const auto key = std::make_pair(dev, k);
+    const auto key = std::make_pair(std::make_pair(dev, k), smem);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, 0) != cudaSuccess || nb < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, smem) != cudaSuccess || nb < 1) {
         (void)cudaGetLastError();
         nb = 1;
     }
@@ -415,9 +415,9 @@ static inline dim3 sblock() { return dim3(kBlock); }
 // sharing the GPU keep their own entries per thread.
 constexpr int kLoopMinPerThread = 4;
 template <class K>
-static inline dim3 lgrid(const Handle& H, long long n, K k) {
+static inline dim3 lgrid(const Handle& H, long long n, K k, size_t smem = 0) {
     const long long cap = std::min<long long>(H.target_blocks,
-                                              (long long)H.nsm * resident_blocks((const void*)k));
+                                              (long long)H.nsm * resident_blocks((const void*)k, smem));
     const long long rows = (n + kBlock - 1) / kBlock;
     long long nb;
     if (H.min_per_thread > 1) {

@@ -340,17 +340,24 @@ class Recorder {
     template <typename... P>
     void launch_coop(const char* name, void (*k)(P...), dim3 grid, dim3 block,
                      typename ident<P>::type... args) {
+        launch_coop_smem(name, k, grid, block, 0, args...);
+    }
+
+    // ... with `smem` bytes of dynamic shared memory per block.
+    template <typename... P>
+    void launch_coop_smem(const char* name, void (*k)(P...), dim3 grid, dim3 block, size_t smem,
+                          typename ident<P>::type... args) {
         if (!ok()) return;
         void* ptrs[sizeof...(P) + 1] = {(void*)&args...};
         if (!graph_) {
-            check(cudaLaunchCooperativeKernel((const void*)k, grid, block, ptrs, 0, stream_), name);
+            check(cudaLaunchCooperativeKernel((const void*)k, grid, block, ptrs, smem, stream_), name);
             return;
         }
         cudaKernelNodeParams p = {};
         p.func = (void*)k;
         p.gridDim = grid;
         p.blockDim = block;
-        p.sharedMemBytes = 0;
+        p.sharedMemBytes = (unsigned)smem;
         p.kernelParams = ptrs;
         cudaGraphNode_t node;
         check(cudaGraphAddKernelNode(&node, graph_, have_last_ ? &last_ : nullptr,

@@ -30,6 +30,8 @@ struct MgOp {
     int tail = 0;                  // first level that one block runs alone in the loop kernel
     std::vector<long long> n;      // entries per level
     void* lev = nullptr;           // device array of the levels' descriptors (FP32 cycle)
+    void* img = nullptr;           // tables of the tail levels in their shared-memory layout
+    std::vector<int> off;          // shared-memory slot offset of each tail level
     float* r32 = nullptr;          // [n_0 + 1] FP32 copy of an FP64 inner residual
     std::vector<void*> bufs;       // every device buffer of the hierarchy
     long long bytes = 0;

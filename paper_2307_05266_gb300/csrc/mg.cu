@@ -28,8 +28,10 @@
 //   coarse levels run on the whole grid with a grid barrier after each phase; on coarse
 //   levels of at most kMgFuseMax entries the restriction and the down stencil are one phase
 //   (each entry re-forms b at its neighbours from their children); the levels from `tail`
-//   down (at most kMgTailMax entries) run in block 0 alone with block barriers while the
-//   other blocks wait at one grid barrier.  Every grid wait is bounded (grid_barrier).
+//   down (at most kMgTailSlots entries together) run in block 0 alone, in its shared memory
+//   (the tables are copied there once per launch), with block barriers, while the other
+//   blocks wait at one grid barrier.  Every grid wait is bounded (grid_barrier).
+#include <cstddef>
 #include <cstring>
 #include <type_traits>
 
@@ -41,9 +43,24 @@ constexpr double kMgOmega = 0.9;
 constexpr double kMgGammaA = 1.3;
 constexpr double kMgGammaS = 1.7;
 constexpr double kMgZeroDiag = 1e-12;
-constexpr long long kMgTailMax = 1024;     // levels with at most this many entries: block 0
 constexpr long long kMgFuseMax = 131072;   // restriction fused into the down stencil
 constexpr int kMgMaxLevels = 40;
+constexpr int kMgTailSlots = 560;          // shared-memory entries of the one-block tail
+constexpr int kMgMaxTail = 16;             // levels in the tail at most
+
+// Block 0's shared-memory copy of the tail levels (levels tail .. nlev-1): slot off[l] + i
+// holds entry i of tail level l, slot off[l] + n_l its zero sentinel.  nb and ch hold
+// level-local indices (ch: into the level below, for every tail level but the first, whose
+// children live on a grid level).  The tables come from a host-built image in global
+// memory with the same layout; b, z, res start at zero.
+struct MgTailSm {
+    float b[kMgTailSlots], z[kMgTailSlots], res[kMgTailSlots];
+    float dg[kMgTailSlots], wd[kMgTailSlots];
+    float w[6][kMgTailSlots];
+    uint16_t nb[6][kMgTailSlots];
+    uint16_t ch[8][kMgTailSlots];
+};
+constexpr size_t kMgTailTables = offsetof(MgTailSm, dg);   // vectors come first
 
 // Device descriptor of one level (FP32).  Every vector has one more entry, kept at 0, that
 // the sentinels of the tables point at (a missing neighbour, a missing child).  Level 0: b
@@ -64,8 +81,10 @@ struct MgLev {
 
 struct MgRun {
     const MgLev* lev;     // [nlev] device descriptors
+    const MgTailSm* img;  // tail image (tables of the tail levels)
     int nlev, tail;
     float gamma;
+    int off[kMgMaxTail];  // slot offset of tail level tail + k
 };
 
 // ---- per-entry work of one phase ----------------------------------------------------------
@@ -230,19 +249,6 @@ __device__ __forceinline__ void fine_phase(const Tabs<float>& t, const Dev& g, c
         }                                                                                   \
     }
 
-// Last level: restriction, exact solve z = wd b, prolongation.
-#define MG_LAST(LOOP, Lp, Fp, gamma)                                                        \
-    {                                                                                       \
-        const uint32_t* __restrict__ ch_ = (Lp)->ch;                                        \
-        const uint32_t ld_ = (Lp)->ld, n_ = (Lp)->n;                                        \
-        const float* __restrict__ wd_ = (Lp)->wd;                                           \
-        LOOP(i, n_) {                                                                       \
-            const float zi = wd_[i] * restrict_at(ch_, ld_, (Fp)->res, i);                  \
-            (Lp)->z[i] = zi;                                                                \
-            prolong_entry((Lp), (Fp), (gamma), zi, i);                                      \
-        }                                                                                   \
-    }
-
 // Coarse level, up: out = y + wd (b - A y), prolonged to the level below.
 #define MG_UP(LOOP, Lp, Fp, gamma)                                                          \
     {                                                                                       \
@@ -266,6 +272,90 @@ __device__ __forceinline__ void fine_phase(const Tabs<float>& t, const Dev& g, c
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
 #define MG_BLOCK_LOOP(i, n) for (uint32_t i = threadIdx.x; i < (n); i += blockDim.x)
 
+// ---- the tail: levels tail .. nlev-1 in block 0's shared memory -----------------------
+
+// Copies the tail tables into shared memory and zeroes its vectors (block 0, once per launch).
+__device__ __forceinline__ void tail_load(MgTailSm& T, const MgTailSm* __restrict__ img) {
+    const uint32_t* src = (const uint32_t*)((const char*)img + kMgTailTables);
+    uint32_t* dst = (uint32_t*)((char*)&T + kMgTailTables);
+    const int nw = (int)((sizeof(MgTailSm) - kMgTailTables) / 4);
+    for (int k = threadIdx.x; k < nw; k += blockDim.x) dst[k] = __ldg(src + k);
+    float* v = (float*)&T;
+    for (int k = threadIdx.x; k < 3 * kMgTailSlots; k += blockDim.x) v[k] = 0.0f;
+    __syncthreads();
+}
+
+// One pass of the tail levels: restriction from the grid level tail - 1, down to the exact
+// solve of the last level, and back up to the prolongation into level tail - 1.
+__device__ __forceinline__ void tail_cycle(MgTailSm& T, const MgRun& M) {
+    const int t = M.tail, nlev = M.nlev;
+    const float gamma = M.gamma;
+    for (int l = t; l < nlev; ++l) {
+        const MgLev* __restrict__ L = M.lev + l;
+        const uint32_t n = L->n;
+        const int o = M.off[l - t];
+        if (l == t) {   // restriction from the grid level below (global memory)
+            const float* __restrict__ resf = M.lev[l - 1].res;
+            MG_BLOCK_LOOP(i, n) {
+                const float b = restrict_at(L->ch, L->ld, resf, i);
+                T.b[o + i] = b;
+                T.z[o + i] = T.wd[o + i] * b;
+            }
+        } else {
+            const int of = M.off[l - 1 - t];
+            MG_BLOCK_LOOP(i, n) {
+                float b = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) b += T.res[of + T.ch[c][o + i]];
+                T.b[o + i] = b;
+                T.z[o + i] = T.wd[o + i] * b;
+            }
+        }
+        __syncthreads();
+        if (l == nlev - 1) break;   // z of the last level is its exact solve
+        MG_BLOCK_LOOP(i, n) {
+            const int k = o + i;
+            float s = T.dg[k] * T.z[k];
+#pragma unroll
+            for (int e = 0; e < 6; ++e) s += T.w[e][k] * T.z[o + T.nb[e][k]];
+            T.res[k] = T.b[k] - s;
+        }
+        __syncthreads();
+    }
+    // up: the correction of level l (its exact solve on the last level, else the post-
+    // smoothed y) prolonged into the level below
+    for (int l = nlev - 1; l >= t; --l) {
+        const MgLev* __restrict__ L = M.lev + l;
+        const uint32_t n = L->n;
+        const int o = M.off[l - t];
+        MG_BLOCK_LOOP(i, n) {
+            const int k = o + i;
+            float out;
+            if (l == nlev - 1) {
+                out = T.z[k];
+            } else {
+                const float y = T.res[k];
+                float s = T.dg[k] * y;
+#pragma unroll
+                for (int e = 0; e < 6; ++e) s += T.w[e][k] * T.res[o + T.nb[e][k]];
+                out = y + T.wd[k] * (T.b[k] - s);
+            }
+            if (l > t) {
+                const int of = M.off[l - 1 - t];
+                const uint32_t nf = L->nfine;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const uint32_t kk = T.ch[c][k];
+                    if (kk < nf) T.res[of + kk] = T.z[of + kk] + gamma * out;
+                }
+            } else {
+                prolong_entry(L, M.lev + (l - 1), gamma, out, i);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // The multigrid-preconditioned CG loop of one inner solve in precision T, after its init
 // kernel (x = 0, r = b, status NOTCONV when b != 0).  r32: the FP32 copy of r that the cycle
 // reads (r itself when T is float).  dS: the diagonal of S-hat (FP64 S stencil).  Same
@@ -283,16 +373,19 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
     __shared__ unsigned s_cont;
     __shared__ Tabs<T> t;
     __shared__ Tabs<float> tf;
+    extern __shared__ __align__(16) unsigned char mg_dyn[];
+    MgTailSm& tsm = *reinterpret_cast<MgTailSm*>(mg_dyn);
     if (gate && *gate) return;
     load_tabs<T>(g, t);
     load_tabs<float>(g, tf);
+    if (blockIdx.x == 0) tail_load(tsm, M.img);
     if (threadIdx.x == 0) s = *st;
     __syncthreads();
     if (s.status != ST_NOTCONV || ld_acquire_u32(&ctl->bar_err) != 0u) return;
     const uint32_t n = (uint32_t)(kS ? C.n_p : C.n_u);
     double* P1 = partials;               // [grid] p.q
     double* P2 = partials + kMaxBlocks;  // [grid][2] r.z, z.z
-    const int nlev = M.nlev, tail = M.tail;
+    const int tail = M.tail;
     const float gamma = M.gamma;
     unsigned target = 0;
     bool ok = true;
@@ -324,21 +417,7 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
             if (!(ok = grid_barrier(ctl, target))) break;
         }
         if (!ok) break;
-        if (blockIdx.x == 0) {
-            for (int l = tail; l < nlev; ++l) {
-                const MgLev* __restrict__ L = M.lev + l;
-                const MgLev* __restrict__ F = M.lev + (l - 1);
-                if (l == nlev - 1) MG_LAST(MG_BLOCK_LOOP, L, F, gamma)
-                else MG_RESTRICT_DOWN(MG_BLOCK_LOOP, L, F)
-                __syncthreads();
-            }
-            for (int l = nlev - 2; l >= tail; --l) {
-                const MgLev* __restrict__ L = M.lev + l;
-                const MgLev* __restrict__ F = M.lev + (l - 1);
-                MG_UP(MG_BLOCK_LOOP, L, F, gamma);
-                __syncthreads();
-            }
-        }
+        if (blockIdx.x == 0) tail_cycle(tsm, M);
         if (!(ok = grid_barrier(ctl, target))) break;
         for (int l = tail - 1; l >= 1; --l) {
             const MgLev* __restrict__ L = M.lev + l;
@@ -669,12 +748,50 @@ int build_hierarchy(Handle& H, MgOp& M, bool simple) {
     const int L = (int)lv.size();
     M.nlev = L;
     M.n.assign(L, 0);
-    M.tail = L - 1;
-    for (int l = 1; l < L; ++l)
-        if (lv[l].n <= kMgTailMax) {
+    // tail: the largest set of last levels whose entries (and one sentinel each) fit the
+    // shared-memory slots, with 16-bit level-local indices (level 0 stays on the grid)
+    M.tail = L;
+    {
+        long long slots = 0;
+        for (int l = L - 1; l >= 1 && L - l <= kMgMaxTail; --l) {
+            slots += lv[l].n + 1;
+            if (slots > kMgTailSlots || lv[l].n >= 65535) break;
             M.tail = l;
-            break;
         }
+    }
+    if (M.tail >= L)
+        return schur_set_error_internal(SCHUR_EINVAL, "multigrid: last level too large");
+    {   // the tail image: tables of the tail levels in their shared-memory layout
+        std::vector<MgTailSm> img(1);
+        std::memset(img.data(), 0, sizeof(MgTailSm));
+        MgTailSm& T = img[0];
+        int o = 0;
+        M.off.clear();
+        for (int l = M.tail; l < L; ++l) {
+            const HostLevel& v = lv[l];
+            M.off.push_back(o);
+            const bool last = (l == L - 1);
+            const std::vector<float> wd = weights(v, last ? 1.0 : kMgOmega);
+            for (long long i = 0; i <= v.n; ++i) {
+                const int k = o + (int)i;
+                for (int e = 0; e < 6; ++e) T.nb[e][k] = (uint16_t)v.n;
+                for (int c = 0; c < 8; ++c) T.ch[c][k] = (uint16_t)(l > M.tail ? lv[l - 1].n : 0);
+                if (i == v.n) continue;
+                T.dg[k] = (float)v.dg[i];
+                T.wd[k] = wd[i];
+                for (int e = 0; e < 6; ++e) {
+                    T.nb[e][k] = (uint16_t)v.nb[e * v.ld + i];
+                    T.w[e][k] = (float)v.w[e * v.ld + i];
+                }
+                if (l > M.tail)
+                    for (int c = 0; c < 8; ++c) T.ch[c][k] = (uint16_t)chs[l][c * v.ld + i];
+            }
+            o += (int)v.n + 1;
+        }
+        MgTailSm* dimg = nullptr;
+        e = upload(M, s, &dimg, img);
+        M.img = dimg;
+    }
     std::vector<MgLev> d((size_t)L);
     for (int l = 0; l < L && e == cudaSuccess; ++l) {
         const HostLevel& v = lv[l];
@@ -743,28 +860,36 @@ void record_mg_loop(Handle& H, Recorder& R, bool simple, bool fp32, void* x, voi
     const Compact C = compact_of(H);
     const long long n = simple ? H.n_p : H.n_u;
     if (!M.nlev) return;   // no entries: the init kernel already finished the solve
-    const MgRun run{(const MgLev*)M.lev, M.nlev, M.tail, (float)(simple ? kMgGammaS : kMgGammaA)};
+    MgRun run;
+    std::memset(&run, 0, sizeof(run));
+    run.lev = (const MgLev*)M.lev;
+    run.img = (const MgTailSm*)M.img;
+    run.nlev = M.nlev;
+    run.tail = M.tail;
+    run.gamma = (float)(simple ? kMgGammaS : kMgGammaA);
+    for (size_t k = 0; k < M.off.size() && k < (size_t)kMgMaxTail; ++k) run.off[k] = M.off[k];
+    const size_t sm = sizeof(MgTailSm);
     if (!fp32) {
         // the cycle reads an FP32 copy of the FP64 residual
         if (simple)
-            R.launch_coop("mgS_loop", k_mg_loop<double, true>, lgrid(H, n, k_mg_loop<double, true>),
-                          sblock(), H.g, C, run, (const double*)H.dSc, (double*)x, (double*)r,
-                          (double*)p, (double*)q, M.r32, H.dctl, st, H.partials, gate);
+            R.launch_coop_smem("mgS_loop", k_mg_loop<double, true>, lgrid(H, n, k_mg_loop<double, true>, sm),
+                               sblock(), sm, H.g, C, run, (const double*)H.dSc, (double*)x, (double*)r,
+                               (double*)p, (double*)q, M.r32, H.dctl, st, H.partials, gate);
         else
-            R.launch_coop("mgA_loop", k_mg_loop<double, false>, lgrid(H, n, k_mg_loop<double, false>),
-                          sblock(), H.g, C, run, (const double*)nullptr, (double*)x, (double*)r,
-                          (double*)p, (double*)q, M.r32, H.dctl, st, H.partials, gate);
+            R.launch_coop_smem("mgA_loop", k_mg_loop<double, false>, lgrid(H, n, k_mg_loop<double, false>, sm),
+                               sblock(), sm, H.g, C, run, (const double*)nullptr, (double*)x, (double*)r,
+                               (double*)p, (double*)q, M.r32, H.dctl, st, H.partials, gate);
     } else {
         // FP32 CG: the cycle reads the residual itself (its level-0 descriptor points at r32,
         // which the kernel does not touch)
         if (simple)
-            R.launch_coop("mgS_loop_f32", k_mg_loop<float, true>, lgrid(H, n, k_mg_loop<float, true>),
-                          sblock(), H.g, C, run, (const float*)nullptr, (float*)x, (float*)r,
-                          (float*)p, (float*)q, (float*)r, H.dctl, st, H.partials, gate);
+            R.launch_coop_smem("mgS_loop_f32", k_mg_loop<float, true>, lgrid(H, n, k_mg_loop<float, true>, sm),
+                               sblock(), sm, H.g, C, run, (const float*)nullptr, (float*)x, (float*)r,
+                               (float*)p, (float*)q, (float*)r, H.dctl, st, H.partials, gate);
         else
-            R.launch_coop("mgA_loop_f32", k_mg_loop<float, false>, lgrid(H, n, k_mg_loop<float, false>),
-                          sblock(), H.g, C, run, (const float*)nullptr, (float*)x, (float*)r,
-                          (float*)p, (float*)q, (float*)r, H.dctl, st, H.partials, gate);
+            R.launch_coop_smem("mgA_loop_f32", k_mg_loop<float, false>, lgrid(H, n, k_mg_loop<float, false>, sm),
+                               sblock(), sm, H.g, C, run, (const float*)nullptr, (float*)x, (float*)r,
+                               (float*)p, (float*)q, (float*)r, H.dctl, st, H.partials, gate);
     }
 }
 
