@@ -309,9 +309,9 @@ __device__ __forceinline__ T phaseS_matvec(const Tabs<T>& t, const Dev& g, const
 }
 
 // Block sum of K doubles, result in every thread (one warp adds through shared memory).
-template <int K>
+template <int K, int NT = kBlock>
 __device__ __forceinline__ void block_sum(double (&v)[K]) {
-    __shared__ double sm[K][kBlock];
+    __shared__ double sm[K][NT];
     __shared__ double out[K];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nthr = blockDim.x;
 #pragma unroll
@@ -335,9 +335,9 @@ __device__ __forceinline__ void block_sum(double (&v)[K]) {
 // Grid sum of K doubles, identical in every block: block sums go to part[block][K], all
 // blocks meet at a barrier, then each block adds the gridDim.x partials in a fixed order.
 // Returns false when the barrier failed.
-template <int K>
+template <int K, int NT = kBlock>
 __device__ __forceinline__ bool grid_sum(double (&v)[K], double* part, Ctl* ctl, unsigned& target) {
-    block_sum<K>(v);
+    block_sum<K, NT>(v);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < K; ++k) part[(size_t)blockIdx.x * K + k] = v[k];
@@ -350,7 +350,7 @@ __device__ __forceinline__ bool grid_sum(double (&v)[K], double* part, Ctl* ctl,
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] += __ldcg(&part[(size_t)i * K + k]);
     }
-    block_sum<K>(acc);
+    block_sum<K, NT>(acc);
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] = acc[k];
     return true;
@@ -376,17 +376,17 @@ static inline dim3 tgrid(const Handle& H) {
     return dim3((unsigned)(nt < H.target_blocks ? nt : H.target_blocks));
 }
 // Resident blocks of kBlock threads per SM for kernel k (cached per device and kernel).
-static int resident_blocks(const void* k, size_t smem = 0) {
+static int resident_blocks(const void* k, size_t smem = 0, int threads = kBlock) {
     static std::mutex mu;
-    static std::map<std::pair<std::pair<int, const void*>, size_t>, int> cache;
+    static std::map<std::pair<std::pair<int, const void*>, std::pair<size_t, int>>, int> cache;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
     std::lock_guard<std::mutex> lock(mu);
-    const auto key = std::make_pair(std::make_pair(dev, k), smem);
+    const auto key = std::make_pair(std::make_pair(dev, k), std::make_pair(smem, threads));
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, smem) != cudaSuccess || nb < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem) != cudaSuccess || nb < 1) {
         (void)cudaGetLastError();
         nb = 1;
     }

@@ -45,7 +45,8 @@ constexpr double kMgGammaS = 1.7;
 constexpr double kMgZeroDiag = 1e-12;
 constexpr long long kMgFuseMax = 131072;   // restriction fused into the down stencil
 constexpr int kMgMaxLevels = 40;
-constexpr int kMgTailSlots = 560;          // shared-memory entries of the one-block tail
+constexpr int kMgBlock = 768;              // threads per block of the loop kernel (1 per SM)
+constexpr int kMgTailSlots = 2400;         // shared-memory entries of the one-block tail
 constexpr int kMgMaxTail = 16;             // levels in the tail at most
 
 // Block 0's shared-memory copy of the tail levels (levels tail .. nlev-1): slot off[l] + i
@@ -441,7 +442,7 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
             v2[0] = (double)a0;
             v2[1] = (double)a1;
         }
-        if (!(ok = grid_sum<2>(v2, P2, ctl, target))) break;
+        if (!(ok = grid_sum<2, kMgBlock>(v2, P2, ctl, target))) break;
         // the first cycle of the kernel starts the iteration (rho, ||z_0||); every later one
         // ends an iteration (count, stop test, beta)
         if (threadIdx.x == 0) {
@@ -473,7 +474,7 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
             else
                 v1[0] = (double)phaseA_matvec<T, U>(t, g, Cl, opaque(pv), opaque(qv));
         }
-        if (!(ok = grid_sum<1>(v1, P1, ctl, target))) break;
+        if (!(ok = grid_sum<1, kMgBlock>(v1, P1, ctl, target))) break;
         if (threadIdx.x == 0) {
             s_cont = matvec_alpha(&s, v1[0]) ? 1u : 0u;
             if (!s_cont) finish_inner(nullptr, &s, 0.0, 0.0);  // counts the iteration
@@ -508,7 +509,7 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
 }
 
 template <typename T, bool kS>
-__global__ void __launch_bounds__(kBlock, 3) k_mg_loop(Dev g, Compact C, MgRun M,
+__global__ void __launch_bounds__(kMgBlock, 1) k_mg_loop(Dev g, Compact C, MgRun M,
                                                        const T* __restrict__ dS, T* __restrict__ xv,
                                                        T* __restrict__ rv, T* __restrict__ pv,
                                                        T* __restrict__ qv, float* __restrict__ r32,
@@ -854,6 +855,23 @@ int mg_prepare(Handle& H, bool simple) {
     return SCHUR_OK;
 }
 
+// Grid of a multigrid loop kernel: one block of kMgBlock threads per SM at most (the
+// kernel's resident blocks with its shared memory, and the launch shape's cap), at least
+// one block per kMgBlock x 4 entries; allows the kernel's dynamic shared memory first.
+template <class K>
+static dim3 mg_grid(const Handle& H, long long n, K k, size_t smem) {
+    static std::mutex mu;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    const long long res = (long long)H.nsm * resident_blocks((const void*)k, smem, kMgBlock);
+    const long long shape = std::max<long long>(1, H.target_blocks / 8);   // blocks_per_sm x nsm / 8
+    const long long want = std::max<long long>(std::min<long long>(H.nsm, (n + kMgBlock - 1) / kMgBlock),
+                                               (n + 4LL * kMgBlock - 1) / (4LL * kMgBlock));
+    return dim3((unsigned)std::max<long long>(1, std::min(std::min(res, shape), want)));
+}
+
 void record_mg_loop(Handle& H, Recorder& R, bool simple, bool fp32, void* x, void* r, void* p,
                     void* q, CgState* st, const int* gate) {
     const MgOp& M = simple ? H.mgS : H.mgA;
@@ -870,25 +888,33 @@ void record_mg_loop(Handle& H, Recorder& R, bool simple, bool fp32, void* x, voi
     for (size_t k = 0; k < M.off.size() && k < (size_t)kMgMaxTail; ++k) run.off[k] = M.off[k];
     const size_t sm = sizeof(MgTailSm);
     if (!fp32) {
+        if (simple) mg_grid(H, n, k_mg_loop<double, true>, sm);
+        else mg_grid(H, n, k_mg_loop<double, false>, sm);
+    } else {
+        if (simple) mg_grid(H, n, k_mg_loop<float, true>, sm);
+        else mg_grid(H, n, k_mg_loop<float, false>, sm);
+    }
+    const dim3 blk(kMgBlock);
+    if (!fp32) {
         // the cycle reads an FP32 copy of the FP64 residual
         if (simple)
-            R.launch_coop_smem("mgS_loop", k_mg_loop<double, true>, lgrid(H, n, k_mg_loop<double, true>, sm),
-                               sblock(), sm, H.g, C, run, (const double*)H.dSc, (double*)x, (double*)r,
+            R.launch_coop_smem("mgS_loop", k_mg_loop<double, true>, mg_grid(H, n, k_mg_loop<double, true>, sm),
+                               blk, sm, H.g, C, run, (const double*)H.dSc, (double*)x, (double*)r,
                                (double*)p, (double*)q, M.r32, H.dctl, st, H.partials, gate);
         else
-            R.launch_coop_smem("mgA_loop", k_mg_loop<double, false>, lgrid(H, n, k_mg_loop<double, false>, sm),
-                               sblock(), sm, H.g, C, run, (const double*)nullptr, (double*)x, (double*)r,
+            R.launch_coop_smem("mgA_loop", k_mg_loop<double, false>, mg_grid(H, n, k_mg_loop<double, false>, sm),
+                               blk, sm, H.g, C, run, (const double*)nullptr, (double*)x, (double*)r,
                                (double*)p, (double*)q, M.r32, H.dctl, st, H.partials, gate);
     } else {
         // FP32 CG: the cycle reads the residual itself (its level-0 descriptor points at r32,
         // which the kernel does not touch)
         if (simple)
-            R.launch_coop_smem("mgS_loop_f32", k_mg_loop<float, true>, lgrid(H, n, k_mg_loop<float, true>, sm),
-                               sblock(), sm, H.g, C, run, (const float*)nullptr, (float*)x, (float*)r,
+            R.launch_coop_smem("mgS_loop_f32", k_mg_loop<float, true>, mg_grid(H, n, k_mg_loop<float, true>, sm),
+                               blk, sm, H.g, C, run, (const float*)nullptr, (float*)x, (float*)r,
                                (float*)p, (float*)q, (float*)r, H.dctl, st, H.partials, gate);
         else
-            R.launch_coop_smem("mgA_loop_f32", k_mg_loop<float, false>, lgrid(H, n, k_mg_loop<float, false>, sm),
-                               sblock(), sm, H.g, C, run, (const float*)nullptr, (float*)x, (float*)r,
+            R.launch_coop_smem("mgA_loop_f32", k_mg_loop<float, false>, mg_grid(H, n, k_mg_loop<float, false>, sm),
+                               blk, sm, H.g, C, run, (const float*)nullptr, (float*)x, (float*)r,
                                (float*)p, (float*)q, (float*)r, H.dctl, st, H.partials, gate);
     }
 }
