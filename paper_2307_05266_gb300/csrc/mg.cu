@@ -45,7 +45,7 @@ constexpr double kMgGammaS = 1.7;
 constexpr double kMgZeroDiag = 1e-12;
 constexpr long long kMgFuseMax = 131072;   // restriction fused into the down stencil
 constexpr int kMgMaxLevels = 40;
-constexpr int kMgBlock = 768;              // threads per block of the loop kernel (1 per SM)
+constexpr int kMgBlock = 1024;             // threads per block of the loop kernel (1 per SM)
 constexpr int kMgTailSlots = 2400;         // shared-memory entries of the one-block tail
 constexpr int kMgMaxTail = 16;             // levels in the tail at most
 
