@@ -111,11 +111,12 @@ def kernel_model(name, nu, npf, d, loop_iters=20, mg=None):
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, bytes) of the
-# hot kernels on this workload from one ncu capture (cold cache) of the kernel sources
-# whose SHA-256 is given; reported as null once the sources differ.
+# hot kernels' timed launches on this workload (ncu over the "timed_kernels" NVTX range of
+# `bench.py --kernels-only --steps 1`, profiles/kernel_traffic_spheres128.md) for the kernel
+# sources whose SHA-256 is given; reported as null once the sources differ.
 NCU_TRAFFIC = {
-    "sources_sha256": "c97a6be6e7867e42d24c943b5ebcd210dbcd8abd5d4c13fd93bc12f99d6e7616",
-    "bytes": {"cgA_dir": 38441256, "cgA_matvec": 76981192, "cgA_update": 75927000, "cgS_dir": 20134000, "cgS_matvec": 36980504, "cgS_update": 33584000, "cgA_dir_f32": 20354000, "cgA_matvec_f32": 66883520, "cgA_update_f32": 38471000, "cgS_dir_f32": 10070000, "cgS_matvec_f32": 26865024, "cgS_update_f32": 16809000, "cgA_loop": 2056728688, "cgS_loop": 67977800, "cgA_loop_f32": 586782840, "cgS_loop_f32": 37546352},
+    "sources_sha256": "1e7b69dd12ce9bd679497aad54ae28e5dfc7ebbbd6d3b610800f5095bec6147f",
+    "bytes": {"cgA_dir": 38444800, "cgA_matvec": 74889472, "cgA_update": 74864896, "cgS_dir": 20138752, "cgS_matvec": 36934400, "cgS_update": 33583104, "cgA_dir_f32": 20354048, "cgA_matvec_f32": 65782272, "cgA_update_f32": 38471936, "cgS_dir_f32": 10070016, "cgS_matvec_f32": 26863872, "cgS_update_f32": 16809472, "cgA_loop": 2084871424, "cgS_loop": 61437440, "cgA_loop_f32": 568776192, "cgS_loop_f32": 36989184, "mgA_loop": 9348999680, "mgS_loop": 970437632, "mgA_loop_f32": 6378373632, "mgS_loop_f32": 389515008},
 }
 
 
