@@ -214,3 +214,34 @@ def test_batch_auto_preconditioner_matches_individual():
     b.close()
     for g in geoms:
         g.close()
+
+
+def test_batch_and_server_with_multigrid_inner_solves():
+    """Multigrid inner solves in the batch graph (persistent loop kernels in parallel
+    branches) and in the server: each result equals the same job solved alone with the same
+    launch shape, and three of them are checked against the oracle's multigrid path."""
+    torch.cuda.set_device(0)
+    masks = _masks()
+    opts = dict(precond=binding.SIMPLE, precision=binding.MIXED, tol=1e-8,
+                inner_precond=binding.INNER_MG)
+    refs = [_alone(m, 0, launch=(2, 16, 1), **opts) for m in masks]
+    geoms = [binding.Geometry(m) for m in masks]
+    b = binding.Batch(geoms, blocks_per_sm=2, **opts)
+    ss, rs, ks = b.run()
+    for i, ref in enumerate(refs):
+        assert ss[i].status == binding.SCHUR_OK
+        assert ss[i].outer_iters == ref[0] and ks[i][0] == ref[2]
+    b.close()
+    for g in geoms:
+        g.close()
+    axes = [0, 1, 2, 0, 1, 2]
+    res, info = _serve(masks, axes, 1 << 36, 6, **opts)
+    for i in ORACLE_MEMBERS:
+        f = [0.0, 0.0, 0.0]
+        f[axes[i]] = 1.0
+        ref = stokes.solve(masks[i], tuple(f), stokes.Options(precond=stokes.SIMPLE, tol=1e-8,
+                                                              inner_precond=stokes.INNER_AMG))
+        k_ref = ref["k"][axes[i]]
+        assert res[i]["status"] == binding.SCHUR_OK
+        assert abs(res[i]["k"] - k_ref) <= 1e-6 * abs(k_ref)
+        assert abs(ks[i][0] - _oracle_k(i, masks[i], 0, stokes.SIMPLE)) <= 1e-6 * abs(ks[i][0])
