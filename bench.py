@@ -353,7 +353,7 @@ def job_rate(ms_local, units_per_rank, world, device):
     return units_per_rank * world / (ms_max / 1e3), ms_max
 
 
-def time_kernels(binding, torch, mask_dev, reps, names=None):
+def time_kernels(binding, torch, mask_dev, reps, names=None, headline=True):
     """Per-kernel timing on a workload: CUDA events around single launches on the
     geometry's stream, L2 flushed before every launch by reading a 512 MiB buffer (clean
     lines, so the timed kernel pays no write-back of the flush), mean over reps - 2 launches;
@@ -373,7 +373,8 @@ def time_kernels(binding, torch, mask_dev, reps, names=None):
     npf = int(info.n_fluid)
     flush = torch.ones(64 * 1024 * 1024, dtype=torch.float64, device="cuda")
     sink = torch.empty((), dtype=torch.float64, device="cuda")
-    traffic_ok = NCU_TRAFFIC["sources_sha256"] == kernel_sources_sha()
+    # the ncu traffic table belongs to the headline workload and the current kernel sources
+    traffic_ok = headline and NCU_TRAFFIC["sources_sha256"] == kernel_sources_sha()
     kern = {}
     torch.cuda.nvtx.range_push("timed_kernels")   # the range ncu captures for the traffic table
     for name in names or binding.KERNELS:
@@ -387,7 +388,14 @@ def time_kernels(binding, torch, mask_dev, reps, names=None):
         tops = ops / (avg / 1e3) / 1e12
         f_hbm, f_alu = gbps / peak_bw, (tops / fp64_peak if wb == 8 else 0.0)
         tr = NCU_TRAFFIC["bytes"].get(name) if traffic_ok else None
+        # the fused-iteration basis of the scope table, (10w + 2) bytes per entry and CG
+        # iteration, for the Jacobi loop kernels
+        s8d = None
+        if name.replace("_f32", "") in ("cgA_loop", "cgS_loop"):
+            ne = nu if "cgA" in name else npf
+            s8d = (10 * wb + 2) * ne * binding.TIMED_LOOP_ITERS / (avg / 1e3) / 1e9 / peak_bw
         kern[name] = {"ms": avg, "iterations": binding.TIMED_LOOP_ITERS if "loop" in name else None,
+                      "frac_hbm_fused_basis": s8d,
                       "alg_bytes": b, "alg_GBps": gbps,
                       "fp64_lane_ops": ops if wb == 8 else 0,
                       "fp64_Tops": tops if wb == 8 else 0.0, "frac_hbm": f_hbm,
@@ -829,7 +837,8 @@ def tight_pattern(binding, torch, mask):
     # loop kernels in the HBM regime: the FP64 A working set (~0.3 GB) exceeds the L2
     kern, _, _, mg, _ = time_kernels(binding, torch, torch.from_numpy(mask).cuda(), 6,
                                      names=["cgA_loop", "cgS_loop", "cgA_loop_f32", "cgS_loop_f32",
-                                            "mgA_loop", "mgS_loop", "mgA_loop_f32", "mgS_loop_f32"])
+                                            "mgA_loop", "mgS_loop", "mgA_loop_f32", "mgS_loop_f32"],
+                                     headline=False)
     out["kernels"] = kern
     out["mg_levels"] = mg
     k64 = out["fp64_simple"]["k"]
