@@ -389,3 +389,25 @@ def test_bounded_barrier_wait_runs_out(cuda, precision):
         st2 = g.solve(**opts)
         g.recover_velocity()
         assert st2.outer_iters == st.outer_iters and g.permeability(0) == k_same
+
+
+@pytest.mark.parametrize("precond", [binding.UZAWA, binding.SIMPLE])
+def test_mixed_history_betas_recorded_by_one_thread(cuda, precond):
+    """The FCG(1) coefficient beta = -z.q / d.q of the mixed-precision outer loop is written
+    to the per-iteration record by the one thread that computed it: the record is finite
+    where formed, repeats bitwise in a second run, and holds each iteration's own value (not
+    the previous one)."""
+    mask = synth.sphere_packing(24, 2.0, 4.0, 0.4, seed=6)
+    hs = []
+    for _ in range(2):
+        with binding.Geometry(mask) as g:
+            st = g.solve(precond=precond, precision=binding.MIXED, tol=1e-9)
+            assert st.status == binding.SCHUR_OK
+            hs.append(g.history())
+    b0, b1 = hs[0]["beta"], hs[1]["beta"]
+    formed = np.isfinite(b0)
+    assert formed.sum() >= 5
+    assert np.array_equal(formed, np.isfinite(b1)) and np.array_equal(b0[formed], b1[formed])
+    seq = b0[formed]
+    assert np.count_nonzero(seq[1:] == seq[:-1]) == 0
+    np.testing.assert_array_equal(hs[0]["alpha"], hs[1]["alpha"])
