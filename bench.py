@@ -60,22 +60,23 @@ DESC = ("spheres128: 128^3 periodic overlapping solid spheres, radii U[4,8), por
 #               binding.TIMED_LOOP_ITERS iterations of the three phases above (timed case)
 # Multigrid-preconditioned CG, one iteration (mgA_loop / mgS_loop; FP32 V-cycle, CG in w),
 # per fine entry, t = 2d * 4 table bytes, f = flag byte (A) or 4-byte face code (S):
-#   x/r update, FP32 residual, z0      read x, p, r, q, wd0; write x, r, (r32,) z0
+#   r update, FP32 residual, z0        read r, q, wd0; write r, (r32,) z0
 #   fine down stencil res0 = r - A z0  read table, f, z0, r32; write res0
-#   fine up stencil z = y + wd0 (...)  read table, f, res0 (= y), r32, wd0, r; write q
-#   direction p = z + beta p           read q, p; write p
+#   fine up stencil z = y + wd0 (...)  read table, f, res0 (= y), r32, wd0, r; write z (FP32)
+#   x += alpha p, p = z + beta p       read z (FP32), p, x; write p, x
 #   matvec q = A p, p.q                read table, f, p (, dS); write q
-# and per coarse entry (FP32): the fused restriction + down stencil reads the children
-# table (32), the 7-point table and coefficients (24 + 24 + 4 + 4), the children's
-# residuals (32) and writes b, z, res (12); the up stencil reads the 7-point table and
-# coefficients, y, b, the children table and the children's z (56 + 8 + 32 + 32) and
-# writes the children's y (32).  FP64 lane-operations: the CG part only (the cycle is FP32).
+# and per coarse entry (FP32): the restriction reads the children table and the children's
+# residuals (32 + 32) and wd, and writes b, z (4 + 8); the down stencil reads the 7-point
+# table and coefficients, the diagonal, z and b (24 + 24 + 4 + 4 + 4) and writes res (4);
+# the up stencil reads the 7-point table and coefficients, y, b, the children table and the
+# children's z (56 + 8 + 32 + 32) and writes the children's y (32).  FP64 lane-operations:
+# the CG part only (the cycle is FP32).
 def mg_model(simple, n0, coarse, d, w):
     t = 2 * d * 4
     f = 4 if simple else 1
-    fine = (6 * w + 4 + (4 if w == 8 else 0) + 4) + (t + f + 8 + 4) + (t + f + 12 + w + w) \
-        + 3 * w + (t + f + w + w + (w if (simple and w == 8) else 0))
-    coarse_b = sum(coarse) * ((32 + 56 + 32 + 12) + (56 + 8 + 32 + 32 + 32))
+    fine = (3 * w + 4 + (4 if w == 8 else 0) + 4) + (t + f + 8 + 4) + (t + f + 12 + w + 4) \
+        + (4 + 4 * w) + (t + f + w + w + (w if (simple and w == 8) else 0))
+    coarse_b = sum(coarse) * ((32 + 32 + 4 + 8) + (24 + 24 + 4 + 4 + 4 + 4) + (56 + 8 + 32 + 32 + 32))
     ops = (2 + 2 + 1 + (8 if simple else 7) + 1) * n0 if w == 8 else 0
     return fine * n0 + coarse_b, ops
 

@@ -121,6 +121,13 @@ template <> struct StreamU<double> { static constexpr int v = 2; };
         }               \
     }
 
+// Hint: fetch the 128-byte line that holds *p into L2.  No register receives data and
+// nothing waits on it, so a stream phase can ask for the entries of a later grid-stride
+// step while its own loads are in flight.  Callers pass in-bounds addresses only.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Row bitmaps of the compact layout.
 struct Compact {
     const uint32_t* ulist;   // [n_u] face index of unknown k
@@ -333,26 +340,35 @@ __device__ __forceinline__ void block_sum(double (&v)[K]) {
 }
 
 // Grid sum of K doubles, identical in every block: block sums go to part[block][K], all
-// blocks meet at a barrier, then each block adds the gridDim.x partials in a fixed order.
-// Returns false when the barrier failed.
+// blocks meet at a barrier, then warp 0 of each block adds the gridDim.x partials in a
+// fixed order (lane l the partials l, l + 32, ..., then a shuffle tree) and shares the
+// totals through shared memory.  Returns false when the barrier failed.
 template <int K, int NT = kBlock>
 __device__ __forceinline__ bool grid_sum(double (&v)[K], double* part, Ctl* ctl, unsigned& target) {
+    __shared__ double tot[K];
     block_sum<K, NT>(v);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < K; ++k) part[(size_t)blockIdx.x * K + k] = v[k];
     }
     if (!grid_barrier(ctl, target)) return false;
-    double acc[K];
+    if (threadIdx.x < 32) {
+        double acc[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = 0.0;
-    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+        for (int k = 0; k < K; ++k) acc[k] = 0.0;
+        for (unsigned i = threadIdx.x; i < gridDim.x; i += 32) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] += __ldcg(&part[(size_t)i * K + k]);
+            for (int k = 0; k < K; ++k) acc[k] += __ldcg(&part[(size_t)i * K + k]);
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            acc[k] = warp_sum(acc[k]);
+            if (threadIdx.x == 0) tot[k] = acc[k];
+        }
     }
-    block_sum<K, NT>(acc);
+    __syncthreads();
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = acc[k];
+    for (int k = 0; k < K; ++k) v[k] = tot[k];
     return true;
 }
 

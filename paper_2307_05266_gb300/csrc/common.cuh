@@ -251,6 +251,13 @@ __device__ __forceinline__ bool reduce_last_block(double (&v)[K], double* partia
 constexpr unsigned kBarrierSpins = 1u << 24;
 constexpr unsigned kBarrierBusy = 1u << 10;
 
+// Arrival at a barrier counter: a release reduction, so that the block's writes (ordered
+// before it by the preceding __syncthreads) are visible to every block whose acquire load
+// reads the count it contributes to.
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -259,21 +266,23 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 
 // All blocks of the grid meet here (the launch is cooperative, so they are co-resident).
 // ctl->bar_count counts arrivals and is zeroed before the launch; `target` is this
-// block's running count of expected arrivals.  A wait that exceeds kBarrierSpins polls,
-// or that sees another block's failure, sets ctl->bar_err and returns false, and the
-// caller leaves its loop: the kernel then ends with an error status instead of hanging.
+// block's running count of expected arrivals.  Thread 0 arrives with a release reduction
+// and waits with acquire loads; the block barriers on both sides extend that ordering to
+// the block's other threads (no full fences).  A wait that exceeds kBarrierSpins polls,
+// or that sees another block's failure (checked every 16th poll), sets ctl->bar_err and
+// returns false, and the caller leaves its loop: the kernel then ends with an error
+// status instead of hanging.
 __device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned& target) {
     __shared__ unsigned s_ok;
     __syncthreads();
     target += gridDim.x;
     if (threadIdx.x == 0) {
         const unsigned limit = ctl->bar_limit ? ctl->bar_limit : kBarrierSpins;
-        __threadfence();
-        if ((int)blockIdx.x + 1 != ctl->bar_skip) atomicAdd(&ctl->bar_count, 1u);
+        if ((int)blockIdx.x + 1 != ctl->bar_skip) red_release_add_u32(&ctl->bar_count, 1u);
         unsigned ok = 1u;
         for (unsigned spin = 0;; ++spin) {
             if ((int)(ld_acquire_u32(&ctl->bar_count) - target) >= 0) break;
-            if (ld_acquire_u32(&ctl->bar_err) != 0u) { ok = 0u; break; }
+            if ((spin & 15u) == 15u && ld_acquire_u32(&ctl->bar_err) != 0u) { ok = 0u; break; }
             if (spin >= limit) {
                 atomicExch(&ctl->bar_err, 1u);
                 ok = 0u;
@@ -281,7 +290,6 @@ __device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned& target) {
             }
             if (spin >= kBarrierBusy) __nanosleep(128);
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();

@@ -28,6 +28,7 @@ struct NvtxRange {
 struct MgOp {
     int nlev = 0;                  // levels including the fine one (0: not built)
     int tail = 0;                  // first level that one block runs alone in the loop kernel
+    int ch16 = 0;                  // the first tail level's children fit 16-bit shared-memory slots
     std::vector<long long> n;      // entries per level
     void* lev = nullptr;           // device array of the levels' descriptors (FP32 cycle)
     void* img = nullptr;           // tables of the tail levels in their shared-memory layout

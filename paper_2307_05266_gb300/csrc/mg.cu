@@ -25,12 +25,12 @@
 //   rule is ||M^-1 r_k|| / ||M^-1 r_0|| < eps as for Jacobi, and the S-hat cycle's output is
 //   not projected (r stays in the range; the solution is projected afterwards).
 // Launch: one persistent cooperative kernel per inner solve.  The fine level and the large
-//   coarse levels run on the whole grid with a grid barrier after each phase; on coarse
-//   levels of at most kMgFuseMax entries the restriction and the down stencil are one phase
-//   (each entry re-forms b at its neighbours from their children); the levels from `tail`
-//   down (at most kMgTailSlots entries together) run in block 0 alone, in its shared memory
-//   (the tables are copied there once per launch), with block barriers, while the other
-//   blocks wait at one grid barrier.  Every grid wait is bounded (grid_barrier).
+//   coarse levels run on the whole grid with a grid barrier after each phase (on a coarse
+//   level: the restriction, the down stencil, and on the way up the post-smoothing with the
+//   prolongation); the levels from `tail` down (at most kMgTailSlots entries together) run
+//   in block 0 alone, in its shared memory (the tables are copied there once per launch),
+//   with block barriers, while the other blocks wait at one grid barrier.  Every grid wait
+//   is bounded (grid_barrier).
 #include <cstddef>
 #include <cstring>
 #include <type_traits>
@@ -43,17 +43,21 @@ constexpr double kMgOmega = 0.9;
 constexpr double kMgGammaA = 1.3;
 constexpr double kMgGammaS = 1.7;
 constexpr double kMgZeroDiag = 1e-12;
-constexpr long long kMgFuseMax = 131072;   // restriction fused into the down stencil
 constexpr int kMgMaxLevels = 40;
 constexpr int kMgBlock = 1024;             // threads per block of the loop kernel (1 per SM)
 constexpr int kMgTailSlots = 2400;         // shared-memory entries of the one-block tail
 constexpr int kMgMaxTail = 16;             // levels in the tail at most
 
+// L2 prefetch distance of the fine-level phases, in grid-stride steps: 1 for FP64 CG vectors
+// (measured 6 % less time per A iteration at 128^3), none for FP32 ones (no gain).
+template <typename T> struct MgPrefetch { static constexpr int v = sizeof(T) == 8 ? 1 : 0; };
+
 // Block 0's shared-memory copy of the tail levels (levels tail .. nlev-1): slot off[l] + i
 // holds entry i of tail level l, slot off[l] + n_l its zero sentinel.  nb and ch hold
-// level-local indices (ch: into the level below, for every tail level but the first, whose
-// children live on a grid level).  The tables come from a host-built image in global
-// memory with the same layout; b, z, res start at zero.
+// level-local indices (ch: into the level below; for the first tail level, whose children
+// live on a grid level, only when that level has at most 65535 entries, MgRun::ch16).  The
+// tables come from a host-built image in global memory with the same layout; b, z, res
+// start at zero.
 struct MgTailSm {
     float b[kMgTailSlots], z[kMgTailSlots], res[kMgTailSlots];
     float dg[kMgTailSlots], wd[kMgTailSlots];
@@ -69,7 +73,7 @@ constexpr size_t kMgTailTables = offsetof(MgTailSm, dg);   // vectors come first
 // and the operator comes from the fine tables (nb, ch, w, dg unused).  res holds the residual after pre-smoothing on the way down and, once the
 // level above has consumed it, y = z + gamma P out_(l+1) on the way up.
 struct MgLev {
-    uint32_t n, ld, nfine, fused;
+    uint32_t n, ld, nfine;
     const uint32_t* nb;   // [6][ld] neighbour entry per direction, n = none
     const uint32_t* ch;   // [8][ld] children at level l - 1, nfine = none
     const float* w;       // [6][ld] off-diagonal coefficients (0 at missing neighbours)
@@ -84,6 +88,7 @@ struct MgRun {
     const MgLev* lev;     // [nlev] device descriptors
     const MgTailSm* img;  // tail image (tables of the tail levels)
     int nlev, tail;
+    int ch16;             // the first tail level's children are in the shared-memory ch table
     float gamma;
     int off[kMgMaxTail];  // slot offset of tail level tail + k
 };
@@ -149,7 +154,7 @@ __device__ __forceinline__ void prolong_entry(const MgLev* __restrict__ L, const
 // their loads issued before the arithmetic (the gathers are latency-bound).  Down:
 // res0 = b0 - Op z0.  Up: the cycle's output y + wd0 (b0 - Op y), y = res0, handed to
 // emit(i, value).
-template <bool kS, bool kUp, int U, class Emit>
+template <bool kS, bool kUp, int U, int PF, class Emit>
 __device__ __forceinline__ void fine_phase(const Tabs<float>& t, const Dev& g, const Compact& C,
                                            const MgLev* __restrict__ L, const float* __restrict__ b,
                                            uint32_t n, Emit emit) {
@@ -160,6 +165,22 @@ __device__ __forceinline__ void fine_phase(const Tabs<float>& t, const Dev& g, c
     const uint32_t* __restrict__ nbt = kS ? C.nbS : C.nbA;
     const long long ldt = kS ? C.ldS : C.ldA;
     WARP_STREAM_BEGIN_U(n, U)
+        if constexpr (PF > 0) {   // the streamed operands of a later step, into L2
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const uint32_t k = idx[j] + PF * step_;
+                if (k < n) {
+#pragma unroll
+                    for (int e = 0; e < 6; ++e)
+                        if (e < ne) prefetch_l2(nbt + e * ldt + k);
+                    if constexpr (kS) prefetch_l2(C.codeS + k);
+                    else prefetch_l2(C.ufl + k);
+                    prefetch_l2(v + k);
+                    prefetch_l2(b + k);
+                    if constexpr (kUp) prefetch_l2(wd + k);
+                }
+            }
+        }
         uint32_t nb[U][6], key[U];
         float vc[U], bc[U], wc[U];
 #pragma unroll
@@ -222,34 +243,6 @@ __device__ __forceinline__ void fine_phase(const Tabs<float>& t, const Dev& g, c
         LOOP(i, n_) res_[i] = b_[i] - coarse_apply(nb_, w_, dg_, ld_, i, z_[i], z_);        \
     }
 
-// Coarse level, restriction and down stencil in one phase: b and z are re-formed at the
-// neighbours from their children.
-#define MG_RESTRICT_DOWN(LOOP, Lp, Fp)                                                      \
-    {                                                                                       \
-        const uint32_t* __restrict__ nb_ = (Lp)->nb;                                        \
-        const uint32_t* __restrict__ ch_ = (Lp)->ch;                                        \
-        const float* __restrict__ w_ = (Lp)->w;                                             \
-        const float* __restrict__ dg_ = (Lp)->dg;                                           \
-        const float* __restrict__ wd_ = (Lp)->wd;                                           \
-        const uint32_t ld_ = (Lp)->ld, n_ = (Lp)->n;                                        \
-        const float* __restrict__ resf_ = (Fp)->res;                                        \
-        float* __restrict__ b_ = (Lp)->b;                                                   \
-        float* __restrict__ z_ = (Lp)->z;                                                   \
-        float* __restrict__ res_ = (Lp)->res;                                               \
-        LOOP(i, n_) {                                                                       \
-            const float bi = restrict_at(ch_, ld_, resf_, i);                               \
-            const float zi = wd_[i] * bi;                                                   \
-            float s_ = dg_[i] * zi;                                                         \
-            _Pragma("unroll 1") for (int e = 0; e < 6; ++e) {                               \
-                const uint32_t j = __ldg(nb_ + e * ld_ + i);                                \
-                s_ += w_[e * ld_ + i] * (wd_[j] * restrict_at(ch_, ld_, resf_, j));         \
-            }                                                                               \
-            b_[i] = bi;                                                                     \
-            z_[i] = zi;                                                                     \
-            res_[i] = bi - s_;                                                              \
-        }                                                                                   \
-    }
-
 // Coarse level, up: out = y + wd (b - A y), prolonged to the level below.
 #define MG_UP(LOOP, Lp, Fp, gamma)                                                          \
     {                                                                                       \
@@ -288,15 +281,36 @@ __device__ __forceinline__ void tail_load(MgTailSm& T, const MgTailSm* __restric
 
 // One pass of the tail levels: restriction from the grid level tail - 1, down to the exact
 // solve of the last level, and back up to the prolongation into level tail - 1.
-__device__ __forceinline__ void tail_cycle(MgTailSm& T, const MgRun& M) {
+__device__ __forceinline__ void tail_cycle(MgTailSm& T, const MgRun& M, const MgLev* lev) {
     const int t = M.tail, nlev = M.nlev;
     const float gamma = M.gamma;
     for (int l = t; l < nlev; ++l) {
-        const MgLev* __restrict__ L = M.lev + l;
+        const MgLev* __restrict__ L = lev + l;
         const uint32_t n = L->n;
         const int o = M.off[l - t];
-        if (l == t) {   // restriction from the grid level below (global memory)
-            const float* __restrict__ resf = M.lev[l - 1].res;
+        if (l == t && M.ch16) {   // restriction from the grid level below (global memory)
+            // two entries per thread and step, so that both sets of gathers are in flight
+            // together; an entry past the end reads the sentinel slot (children = the zero
+            // entry of the level below) and is not stored
+            const float* __restrict__ resf = lev[l - 1].res;
+            for (uint32_t i = threadIdx.x; i < n; i += 2 * blockDim.x) {
+                const uint32_t i2 = i + blockDim.x;
+                const int k1 = o + (int)i, k2 = o + (int)(i2 < n ? i2 : n);
+                float b1 = 0.0f, b2 = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    b1 += resf[T.ch[c][k1]];
+                    b2 += resf[T.ch[c][k2]];
+                }
+                T.b[k1] = b1;
+                T.z[k1] = T.wd[k1] * b1;
+                if (i2 < n) {
+                    T.b[k2] = b2;
+                    T.z[k2] = T.wd[k2] * b2;
+                }
+            }
+        } else if (l == t) {
+            const float* __restrict__ resf = lev[l - 1].res;
             MG_BLOCK_LOOP(i, n) {
                 const float b = restrict_at(L->ch, L->ld, resf, i);
                 T.b[o + i] = b;
@@ -326,7 +340,7 @@ __device__ __forceinline__ void tail_cycle(MgTailSm& T, const MgRun& M) {
     // up: the correction of level l (its exact solve on the last level, else the post-
     // smoothed y) prolonged into the level below
     for (int l = nlev - 1; l >= t; --l) {
-        const MgLev* __restrict__ L = M.lev + l;
+        const MgLev* __restrict__ L = lev + l;
         const uint32_t n = L->n;
         const int o = M.off[l - t];
         MG_BLOCK_LOOP(i, n) {
@@ -349,8 +363,18 @@ __device__ __forceinline__ void tail_cycle(MgTailSm& T, const MgRun& M) {
                     const uint32_t kk = T.ch[c][k];
                     if (kk < nf) T.res[of + kk] = T.z[of + kk] + gamma * out;
                 }
+            } else if (M.ch16) {
+                const MgLev* __restrict__ F = lev + (l - 1);
+                const uint32_t nf = L->nfine;
+                const float* __restrict__ zf = F->z;
+                float* __restrict__ yf = F->res;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const uint32_t kk = T.ch[c][k];
+                    if (kk < nf) yf[kk] = zf[kk] + gamma * out;
+                }
             } else {
-                prolong_entry(L, M.lev + (l - 1), gamma, out, i);
+                prolong_entry(L, lev + (l - 1), gamma, out, i);
             }
         }
         __syncthreads();
@@ -370,13 +394,24 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
                                         float* __restrict__ r32, Ctl* ctl, CgState* st,
                                         double* partials, const int* gate) {
     constexpr bool kSame = std::is_same<T, float>::value;
+    constexpr int PF = MgPrefetch<T>::v;
     __shared__ CgState s;
     __shared__ unsigned s_cont;
     __shared__ Tabs<T> t;
     __shared__ Tabs<float> tf;
+    // the level descriptors, copied once per launch: every phase starts from its level's
+    // fields, and a global load there would put one dependent round trip before each phase
+    __shared__ MgLev lev[kMgMaxLevels];
     extern __shared__ __align__(16) unsigned char mg_dyn[];
     MgTailSm& tsm = *reinterpret_cast<MgTailSm*>(mg_dyn);
     if (gate && *gate) return;
+    {
+        static_assert(sizeof(MgLev) % 4 == 0, "descriptor copy by 32-bit words");
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(M.lev);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(lev);
+        const int nw = M.nlev * (int)(sizeof(MgLev) / 4);
+        for (int k = threadIdx.x; k < nw; k += blockDim.x) dst[k] = __ldg(src + k);
+    }
     load_tabs<T>(g, t);
     load_tabs<float>(g, tf);
     if (blockIdx.x == 0) tail_load(tsm, M.img);
@@ -391,9 +426,10 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
     unsigned target = 0;
     bool ok = true;
     bool started = false;
+    T alpha_prev = (T)0;   // the step x += alpha_prev p not yet applied
     {   // the FP32 residual and z0 = wd0 r for the first cycle (later: with the r update)
-        const float* __restrict__ wd0 = M.lev[0].wd;
-        float* __restrict__ z0 = M.lev[0].z;
+        const float* __restrict__ wd0 = lev[0].wd;
+        float* __restrict__ z0 = lev[0].z;
         MG_GRID_LOOP(i, n) {
             const float ri = (float)rv[i];
             if constexpr (!kSame) r32[i] = ri;
@@ -403,39 +439,37 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
     for (;;) {
         // ---- V-cycle on r (r32 and z0 complete after this barrier)
         if (!(ok = grid_barrier(ctl, target))) break;
-        fine_phase<kS, false, 1>(tf, g, C, M.lev, r32, n, [](uint32_t, float) {});
+        fine_phase<kS, false, 1, PF>(tf, g, C, lev, r32, n, [](uint32_t, float) {});
         if (!(ok = grid_barrier(ctl, target))) break;
         for (int l = 1; l < tail; ++l) {
-            const MgLev* __restrict__ L = M.lev + l;
-            const MgLev* __restrict__ F = M.lev + (l - 1);
-            if (L->fused) {
-                MG_RESTRICT_DOWN(MG_GRID_LOOP, L, F);
-            } else {
-                MG_RESTRICT(MG_GRID_LOOP, L, F);
-                if (!(ok = grid_barrier(ctl, target))) break;
-                MG_DOWN(MG_GRID_LOOP, L);
-            }
+            const MgLev* __restrict__ L = lev + l;
+            const MgLev* __restrict__ F = lev + (l - 1);
+            MG_RESTRICT(MG_GRID_LOOP, L, F);
+            if (!(ok = grid_barrier(ctl, target))) break;
+            MG_DOWN(MG_GRID_LOOP, L);
             if (!(ok = grid_barrier(ctl, target))) break;
         }
         if (!ok) break;
-        if (blockIdx.x == 0) tail_cycle(tsm, M);
+        if (blockIdx.x == 0) tail_cycle(tsm, M, lev);
         if (!(ok = grid_barrier(ctl, target))) break;
         for (int l = tail - 1; l >= 1; --l) {
-            const MgLev* __restrict__ L = M.lev + l;
-            const MgLev* __restrict__ F = M.lev + (l - 1);
+            const MgLev* __restrict__ L = lev + l;
+            const MgLev* __restrict__ F = lev + (l - 1);
             MG_UP(MG_GRID_LOOP, L, F, gamma);
             if (!(ok = grid_barrier(ctl, target))) break;
         }
         if (!ok) break;
-        // ---- z = the cycle's output (into q), r.z and z.z
+        // ---- z = the cycle's output, r.z and z.z.  z is an FP32 value (exact in T), kept
+        // in the level-0 z buffer: z0 is consumed by the prolongation into level 0 above and
+        // formed again by the update below
         double v2[2];
         {
             T a0 = (T)0, a1 = (T)0;
-            T* __restrict__ q = qv;
+            float* __restrict__ zout = lev[0].z;
             const T* __restrict__ r = rv;
-            fine_phase<kS, true, 1>(tf, g, C, M.lev, r32, n, [&](uint32_t i, float zf32) {
+            fine_phase<kS, true, 1, PF>(tf, g, C, lev, r32, n, [&](uint32_t i, float zf32) {
                 const T zf = (T)zf32;
-                q[i] = zf;
+                zout[i] = zf32;
                 a0 += r[i] * zf;
                 a1 += zf * zf;
             });
@@ -452,12 +486,26 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
         __syncthreads();
         started = true;
         if (!s_cont) break;
-        // ---- p = z + beta p
+        // ---- x += alpha_prev p (the previous iteration's step, deferred so that p is read
+        // once), then p = z + beta p
         {
             const T beta = (T)(s.first ? 0.0 : s.beta);
+            const T ap = alpha_prev;
             T* __restrict__ p = opaque(pv);
-            const T* __restrict__ z = opaque(qv);
-            MG_GRID_LOOP(i, n) p[i] = z[i] + beta * p[i];
+            T* __restrict__ x = opaque(xv);
+            const float* __restrict__ z = opaque(lev[0].z);
+            const uint32_t ahead = PF * gridDim.x * blockDim.x;
+            MG_GRID_LOOP(i, n) {
+                if (PF > 0 && i + ahead < n) {
+                    prefetch_l2(z + i + ahead);
+                    prefetch_l2(p + i + ahead);
+                    prefetch_l2(x + i + ahead);
+                }
+                const T pi = p[i];
+                x[i] += ap * pi;
+                p[i] = (T)z[i] + beta * pi;
+            }
+            alpha_prev = (T)0;
         }
         if (!(ok = grid_barrier(ctl, target))) break;
         // ---- q = Op p, p.q
@@ -481,25 +529,39 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
         }
         __syncthreads();
         if (!s_cont) break;
-        // ---- x += alpha p, r -= alpha q, the FP32 residual and z0 = wd0 r
+        // ---- r -= alpha q, the FP32 residual and z0 = wd0 r (x += alpha p: next direction
+        // phase, or after the loop)
         {
             const T alpha = (T)s.alpha;
-            T* __restrict__ x = opaque(xv);
             T* __restrict__ r = opaque(rv);
-            const T* __restrict__ p = opaque(pv);
             const T* __restrict__ q = opaque(qv);
-            const float* __restrict__ w0 = opaque(M.lev[0].wd);
-            float* __restrict__ z0 = opaque(M.lev[0].z);
+            const float* __restrict__ w0 = opaque(lev[0].wd);
+            float* __restrict__ z0 = opaque(lev[0].z);
             float* __restrict__ rf = opaque(r32);
+            const uint32_t ahead = PF * gridDim.x * blockDim.x;
             MG_GRID_LOOP(i, n) {
-                x[i] += alpha * p[i];
+                if (PF > 0 && i + ahead < n) {
+                    const uint32_t k = i + ahead;
+                    prefetch_l2(r + k);
+                    prefetch_l2(q + k);
+                    prefetch_l2(w0 + k);
+                }
                 const T ri = r[i] - alpha * q[i];
                 r[i] = ri;
                 const float r32i = (float)ri;
                 if constexpr (!kSame) rf[i] = r32i;
                 z0[i] = w0[i] * r32i;
             }
+            alpha_prev = alpha;
         }
+    }
+    // the last iteration's step x += alpha p (p is unchanged since its update phase; no
+    // barrier is needed: the kernel ends here)
+    if (ok && alpha_prev != (T)0) {
+        const T ap = alpha_prev;
+        T* __restrict__ x = opaque(xv);
+        const T* __restrict__ p = opaque(pv);
+        MG_GRID_LOOP(i, n) x[i] += ap * p[i];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (!ok) s.status = ST_BARRIER;
@@ -762,6 +824,9 @@ int build_hierarchy(Handle& H, MgOp& M, bool simple) {
     }
     if (M.tail >= L)
         return schur_set_error_internal(SCHUR_EINVAL, "multigrid: last level too large");
+    // the first tail level's children as 16-bit indices when the grid level below has at
+    // most 65535 entries (its sentinel index included)
+    M.ch16 = lv[M.tail - 1].n <= 65535 ? 1 : 0;
     {   // the tail image: tables of the tail levels in their shared-memory layout
         std::vector<MgTailSm> img(1);
         std::memset(img.data(), 0, sizeof(MgTailSm));
@@ -776,7 +841,8 @@ int build_hierarchy(Handle& H, MgOp& M, bool simple) {
             for (long long i = 0; i <= v.n; ++i) {
                 const int k = o + (int)i;
                 for (int e = 0; e < 6; ++e) T.nb[e][k] = (uint16_t)v.n;
-                for (int c = 0; c < 8; ++c) T.ch[c][k] = (uint16_t)(l > M.tail ? lv[l - 1].n : 0);
+                const bool has_ch = l > M.tail || M.ch16;
+                for (int c = 0; c < 8; ++c) T.ch[c][k] = (uint16_t)(has_ch ? lv[l - 1].n : 0);
                 if (i == v.n) continue;
                 T.dg[k] = (float)v.dg[i];
                 T.wd[k] = wd[i];
@@ -784,7 +850,7 @@ int build_hierarchy(Handle& H, MgOp& M, bool simple) {
                     T.nb[e][k] = (uint16_t)v.nb[e * v.ld + i];
                     T.w[e][k] = (float)v.w[e * v.ld + i];
                 }
-                if (l > M.tail)
+                if (has_ch)
                     for (int c = 0; c < 8; ++c) T.ch[c][k] = (uint16_t)chs[l][c * v.ld + i];
             }
             o += (int)v.n + 1;
@@ -802,7 +868,6 @@ int build_hierarchy(Handle& H, MgOp& M, bool simple) {
         dl.n = (uint32_t)v.n;
         dl.ld = (uint32_t)v.ld;
         dl.nfine = l > 0 ? (uint32_t)lv[l - 1].n : 0u;
-        dl.fused = v.n <= kMgFuseMax ? 1u : 0u;
         const bool last = (l == L - 1);
         float *wd = nullptr, *w = nullptr, *dg = nullptr;
         uint32_t *nb = nullptr, *ch = nullptr;
@@ -884,6 +949,7 @@ void record_mg_loop(Handle& H, Recorder& R, bool simple, bool fp32, void* x, voi
     run.img = (const MgTailSm*)M.img;
     run.nlev = M.nlev;
     run.tail = M.tail;
+    run.ch16 = M.ch16;
     run.gamma = (float)(simple ? kMgGammaS : kMgGammaA);
     for (size_t k = 0; k < M.off.size() && k < (size_t)kMgMaxTail; ++k) run.off[k] = M.off[k];
     const size_t sm = sizeof(MgTailSm);
