@@ -62,8 +62,10 @@ DESC = ("spheres128: 128^3 periodic overlapping solid spheres, radii U[4,8), por
 # per fine entry, t = 2d * 4 table bytes, f = flag byte (A) or 4-byte face code (S):
 #   r update, FP32 residual, z0        read r, q, wd0; write r, (r32,) z0
 #   fine down stencil res0 = r - A z0  read table, f, z0, r32; write res0
-#   fine up stencil z = y + wd0 (...)  read table, f, res0 (= y), r32, wd0, r; write z (FP32)
-#   x += alpha p, p = z + beta p       read z (FP32), p, x; write p, x
+#   x += alpha p (during the tail)     read x, p; write x
+#   fine up stencil z = y + wd0 (...)  read table, f, res0 (= y), r32, wd0, r; write z
+#                                      (FP32 for an FP64 CG, in w for an FP32 one)
+#   direction p = z + beta p           read z, p; write p
 #   matvec q = A p, p.q                read table, f, p (, dS); write q
 # and per coarse entry (FP32): the restriction reads the children table and the children's
 # residuals (32 + 32) and wd, and writes b, z (4 + 8); the down stencil reads the 7-point
@@ -74,8 +76,9 @@ DESC = ("spheres128: 128^3 periodic overlapping solid spheres, radii U[4,8), por
 def mg_model(simple, n0, coarse, d, w):
     t = 2 * d * 4
     f = 4 if simple else 1
-    fine = (3 * w + 4 + (4 if w == 8 else 0) + 4) + (t + f + 8 + 4) + (t + f + 12 + w + 4) \
-        + (4 + 4 * w) + (t + f + w + w + (w if (simple and w == 8) else 0))
+    z = 4 if w == 8 else w   # bytes of the stored cycle output
+    fine = (3 * w + 4 + (4 if w == 8 else 0) + 4) + (t + f + 8 + 4) + 3 * w + (t + f + 12 + w + z) \
+        + (z + 2 * w) + (t + f + w + w + (w if (simple and w == 8) else 0))
     coarse_b = sum(coarse) * ((32 + 32 + 4 + 8) + (24 + 24 + 4 + 4 + 4 + 4) + (56 + 8 + 32 + 32 + 32))
     ops = (2 + 2 + 1 + (8 if simple else 7) + 1) * n0 if w == 8 else 0
     return fine * n0 + coarse_b, ops

@@ -395,6 +395,9 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
                                         double* partials, const int* gate) {
     constexpr bool kSame = std::is_same<T, float>::value;
     constexpr int PF = MgPrefetch<T>::v;
+    // FP64 CG vectors: the cycle's output z stays FP32 (exact in T) in the level-0 z buffer,
+    // half the bytes of q; FP32 ones: z in q.
+    constexpr bool kZ32 = !kSame;
     __shared__ CgState s;
     __shared__ unsigned s_cont;
     __shared__ Tabs<T> t;
@@ -426,7 +429,10 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
     unsigned target = 0;
     bool ok = true;
     bool started = false;
-    T alpha_prev = (T)0;   // the step x += alpha_prev p not yet applied
+    // The step x += alpha p of an iteration is taken in the next cycle, by the blocks that
+    // wait at the grid barrier while block 0 runs the tail levels: nothing in the cycle
+    // reads x, and p keeps its value until the direction phase after the cycle.
+    T alpha_prev = (T)0;   // the step x += alpha_prev p not yet taken
     {   // the FP32 residual and z0 = wd0 r for the first cycle (later: with the r update)
         const float* __restrict__ wd0 = lev[0].wd;
         float* __restrict__ z0 = lev[0].z;
@@ -451,6 +457,24 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
         }
         if (!ok) break;
         if (blockIdx.x == 0) tail_cycle(tsm, M, lev);
+        if (alpha_prev != (T)0 && (blockIdx.x > 0 || gridDim.x == 1)) {
+            // x += alpha_prev p: blocks 1 .. grid - 1 (block 0 alone on a one-block grid)
+            const T ap = alpha_prev;
+            T* __restrict__ x = opaque(xv);
+            const T* __restrict__ p = opaque(pv);
+            const uint32_t nb = gridDim.x > 1 ? gridDim.x - 1 : 1u;
+            const uint32_t b = gridDim.x > 1 ? blockIdx.x - 1 : 0u;
+            const uint32_t stride = nb * blockDim.x;
+            const uint32_t ahead = PF * stride;
+            for (uint32_t i = b * blockDim.x + threadIdx.x; i < n; i += stride) {
+                if (PF > 0 && i + ahead < n) {
+                    prefetch_l2(x + i + ahead);
+                    prefetch_l2(p + i + ahead);
+                }
+                x[i] += ap * p[i];
+            }
+        }
+        alpha_prev = (T)0;
         if (!(ok = grid_barrier(ctl, target))) break;
         for (int l = tail - 1; l >= 1; --l) {
             const MgLev* __restrict__ L = lev + l;
@@ -459,17 +483,19 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
             if (!(ok = grid_barrier(ctl, target))) break;
         }
         if (!ok) break;
-        // ---- z = the cycle's output, r.z and z.z.  z is an FP32 value (exact in T), kept
-        // in the level-0 z buffer: z0 is consumed by the prolongation into level 0 above and
-        // formed again by the update below
+        // ---- z = the cycle's output, r.z and z.z.  kZ32: z is an FP32 value (exact in T),
+        // kept in the level-0 z buffer (z0 was consumed by the prolongation into level 0
+        // above and is formed again by the update below); else in q
         double v2[2];
         {
             T a0 = (T)0, a1 = (T)0;
             float* __restrict__ zout = lev[0].z;
+            T* __restrict__ q = qv;
             const T* __restrict__ r = rv;
             fine_phase<kS, true, 1, PF>(tf, g, C, lev, r32, n, [&](uint32_t i, float zf32) {
                 const T zf = (T)zf32;
-                zout[i] = zf32;
+                if constexpr (kZ32) zout[i] = zf32;
+                else q[i] = zf;
                 a0 += r[i] * zf;
                 a1 += zf * zf;
             });
@@ -486,26 +512,24 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
         __syncthreads();
         started = true;
         if (!s_cont) break;
-        // ---- x += alpha_prev p (the previous iteration's step, deferred so that p is read
-        // once), then p = z + beta p
-        {
+        // ---- p = z + beta p
+        if constexpr (kZ32) {
             const T beta = (T)(s.first ? 0.0 : s.beta);
-            const T ap = alpha_prev;
             T* __restrict__ p = opaque(pv);
-            T* __restrict__ x = opaque(xv);
             const float* __restrict__ z = opaque(lev[0].z);
             const uint32_t ahead = PF * gridDim.x * blockDim.x;
             MG_GRID_LOOP(i, n) {
                 if (PF > 0 && i + ahead < n) {
                     prefetch_l2(z + i + ahead);
                     prefetch_l2(p + i + ahead);
-                    prefetch_l2(x + i + ahead);
                 }
-                const T pi = p[i];
-                x[i] += ap * pi;
-                p[i] = (T)z[i] + beta * pi;
+                p[i] = (T)z[i] + beta * p[i];
             }
-            alpha_prev = (T)0;
+        } else {
+            const T beta = (T)(s.first ? 0.0 : s.beta);
+            T* __restrict__ p = opaque(pv);
+            const T* __restrict__ z = opaque(qv);
+            MG_GRID_LOOP(i, n) p[i] = z[i] + beta * p[i];
         }
         if (!(ok = grid_barrier(ctl, target))) break;
         // ---- q = Op p, p.q
@@ -529,8 +553,7 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
         }
         __syncthreads();
         if (!s_cont) break;
-        // ---- r -= alpha q, the FP32 residual and z0 = wd0 r (x += alpha p: next direction
-        // phase, or after the loop)
+        // ---- r -= alpha q, the FP32 residual and z0 = wd0 r (x += alpha p: next cycle)
         {
             const T alpha = (T)s.alpha;
             T* __restrict__ r = opaque(rv);
@@ -555,8 +578,8 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
             alpha_prev = alpha;
         }
     }
-    // the last iteration's step x += alpha p (p is unchanged since its update phase; no
-    // barrier is needed: the kernel ends here)
+    // a step x += alpha p still due (the loop ends after a cycle, which has taken it, so this
+    // is a safeguard; p is unchanged since its update phase, and the kernel ends here)
     if (ok && alpha_prev != (T)0) {
         const T ap = alpha_prev;
         T* __restrict__ x = opaque(xv);
