@@ -119,8 +119,8 @@ def kernel_model(name, nu, npf, d, loop_iters=20, mg=None):
 # `bench.py --kernels-only --steps 1`, profiles/kernel_traffic_spheres128.md) for the kernel
 # sources whose SHA-256 is given; reported as null once the sources differ.
 NCU_TRAFFIC = {
-    "sources_sha256": "1e7b69dd12ce9bd679497aad54ae28e5dfc7ebbbd6d3b610800f5095bec6147f",
-    "bytes": {"cgA_dir": 38444800, "cgA_matvec": 74889472, "cgA_update": 74864896, "cgS_dir": 20138752, "cgS_matvec": 36934400, "cgS_update": 33583104, "cgA_dir_f32": 20354048, "cgA_matvec_f32": 65782272, "cgA_update_f32": 38471936, "cgS_dir_f32": 10070016, "cgS_matvec_f32": 26863872, "cgS_update_f32": 16809472, "cgA_loop": 2084871424, "cgS_loop": 61437440, "cgA_loop_f32": 568776192, "cgS_loop_f32": 36989184, "mgA_loop": 9348999680, "mgS_loop": 970437632, "mgA_loop_f32": 6378373632, "mgS_loop_f32": 389515008},
+    "sources_sha256": "06aa1e0ea591e6e198be929ce73cfacc906e4ec43ee6db524c2c8082abdb3611",
+    "bytes": {"cgA_dir": 38442752, "cgA_matvec": 74835712, "cgA_update": 74826496, "cgS_dir": 20134656, "cgS_matvec": 36942336, "cgS_update": 33583616, "cgA_dir_f32": 20354048, "cgA_matvec_f32": 65732352, "cgA_update_f32": 38471168, "cgS_dir_f32": 10069504, "cgS_matvec_f32": 26888192, "cgS_update_f32": 16808960, "cgA_loop": 2074676992, "cgS_loop": 61906944, "cgA_loop_f32": 567348992, "cgS_loop_f32": 36978944, "mgA_loop": 9430959104, "mgS_loop": 1215778304, "mgA_loop_f32": 6353433856, "mgS_loop_f32": 268300032},
 }
 
 
