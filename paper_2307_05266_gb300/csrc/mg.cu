@@ -44,7 +44,14 @@ constexpr double kMgGammaA = 1.3;
 constexpr double kMgGammaS = 1.7;
 constexpr double kMgZeroDiag = 1e-12;
 constexpr int kMgMaxLevels = 40;
-constexpr int kMgBlock = 1024;             // threads per block of the loop kernel (1 per SM)
+// Threads per block of the loop kernel (one block per SM) for CG vectors of type T on the
+// operator A (kS false) or S-hat.  The register budget per thread is 65536 / threads; with
+// 1024 threads (64 registers) the kernel spills.  Measured at 128^3 (time per iteration
+// against 1024 threads): FP64 A 768 threads (80 registers) -2 %, 640 +7 %, 896 +12 %;
+// FP64 S-hat 640 threads -6 %; FP32 A and S-hat 896 threads (72 registers) -7 %.
+template <typename T, bool kS> struct MgBlock {
+    static constexpr int v = sizeof(T) == 8 ? (kS ? 640 : 768) : 896;
+};
 constexpr int kMgTailSlots = 2400;         // shared-memory entries of the one-block tail
 constexpr int kMgMaxTail = 16;             // levels in the tail at most
 
@@ -395,6 +402,7 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
                                         double* partials, const int* gate) {
     constexpr bool kSame = std::is_same<T, float>::value;
     constexpr int PF = MgPrefetch<T>::v;
+    constexpr int NT = MgBlock<T, kS>::v;
     // FP64 CG vectors: the cycle's output z stays FP32 (exact in T) in the level-0 z buffer,
     // half the bytes of q; FP32 ones: z in q.
     constexpr bool kZ32 = !kSame;
@@ -502,7 +510,7 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
             v2[0] = (double)a0;
             v2[1] = (double)a1;
         }
-        if (!(ok = grid_sum<2, kMgBlock>(v2, P2, ctl, target))) break;
+        if (!(ok = grid_sum<2, NT>(v2, P2, ctl, target))) break;
         // the first cycle of the kernel starts the iteration (rho, ||z_0||); every later one
         // ends an iteration (count, stop test, beta)
         if (threadIdx.x == 0) {
@@ -540,13 +548,15 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
             Cl.nbS = opaque(C.nbS);
             Cl.codeS = opaque(C.codeS);
             Cl.ufl = opaque(C.ufl);
-            constexpr int U = LoopMvU<T>::v;
+            // one entry per thread and step: in this 64-register kernel the two-entry form of
+            // the Jacobi loops spills (measured 7 % more time per FP64 A iteration at 128^3)
+            constexpr int U = 1;
             if constexpr (kS)
                 v1[0] = (double)phaseS_matvec<T, U>(t, g, Cl, opaque(dS), opaque(pv), opaque(qv));
             else
                 v1[0] = (double)phaseA_matvec<T, U>(t, g, Cl, opaque(pv), opaque(qv));
         }
-        if (!(ok = grid_sum<1, kMgBlock>(v1, P1, ctl, target))) break;
+        if (!(ok = grid_sum<1, NT>(v1, P1, ctl, target))) break;
         if (threadIdx.x == 0) {
             s_cont = matvec_alpha(&s, v1[0]) ? 1u : 0u;
             if (!s_cont) finish_inner(nullptr, &s, 0.0, 0.0);  // counts the iteration
@@ -594,7 +604,7 @@ __device__ __forceinline__ void mg_loop(const Dev& g, const Compact& C, const Mg
 }
 
 template <typename T, bool kS>
-__global__ void __launch_bounds__(kMgBlock, 1) k_mg_loop(Dev g, Compact C, MgRun M,
+__global__ void __launch_bounds__(MgBlock<T, kS>::v, 1) k_mg_loop(Dev g, Compact C, MgRun M,
                                                        const T* __restrict__ dS, T* __restrict__ xv,
                                                        T* __restrict__ rv, T* __restrict__ pv,
                                                        T* __restrict__ qv, float* __restrict__ r32,
@@ -943,20 +953,20 @@ int mg_prepare(Handle& H, bool simple) {
     return SCHUR_OK;
 }
 
-// Grid of a multigrid loop kernel: one block of kMgBlock threads per SM at most (the
+// Grid of a multigrid loop kernel of `nt` threads per block: one block per SM at most (the
 // kernel's resident blocks with its shared memory, and the launch shape's cap), at least
-// one block per kMgBlock x 4 entries; allows the kernel's dynamic shared memory first.
+// one block per nt x 4 entries; allows the kernel's dynamic shared memory first.
 template <class K>
-static dim3 mg_grid(const Handle& H, long long n, K k, size_t smem) {
+static dim3 mg_grid(const Handle& H, long long n, K k, size_t smem, int nt) {
     static std::mutex mu;
     {
         std::lock_guard<std::mutex> lock(mu);
         cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
-    const long long res = (long long)H.nsm * resident_blocks((const void*)k, smem, kMgBlock);
+    const long long res = (long long)H.nsm * resident_blocks((const void*)k, smem, nt);
     const long long shape = std::max<long long>(1, H.target_blocks / 8);   // blocks_per_sm x nsm / 8
-    const long long want = std::max<long long>(std::min<long long>(H.nsm, (n + kMgBlock - 1) / kMgBlock),
-                                               (n + 4LL * kMgBlock - 1) / (4LL * kMgBlock));
+    const long long want = std::max<long long>(std::min<long long>(H.nsm, (n + nt - 1) / nt),
+                                               (n + 4LL * nt - 1) / (4LL * nt));
     return dim3((unsigned)std::max<long long>(1, std::min(std::min(res, shape), want)));
 }
 
@@ -976,34 +986,28 @@ void record_mg_loop(Handle& H, Recorder& R, bool simple, bool fp32, void* x, voi
     run.gamma = (float)(simple ? kMgGammaS : kMgGammaA);
     for (size_t k = 0; k < M.off.size() && k < (size_t)kMgMaxTail; ++k) run.off[k] = M.off[k];
     const size_t sm = sizeof(MgTailSm);
-    if (!fp32) {
-        if (simple) mg_grid(H, n, k_mg_loop<double, true>, sm);
-        else mg_grid(H, n, k_mg_loop<double, false>, sm);
-    } else {
-        if (simple) mg_grid(H, n, k_mg_loop<float, true>, sm);
-        else mg_grid(H, n, k_mg_loop<float, false>, sm);
-    }
-    const dim3 blk(kMgBlock);
+    constexpr int ntAd = MgBlock<double, false>::v, ntSd = MgBlock<double, true>::v;
+    constexpr int ntAf = MgBlock<float, false>::v, ntSf = MgBlock<float, true>::v;
     if (!fp32) {
         // the cycle reads an FP32 copy of the FP64 residual
         if (simple)
-            R.launch_coop_smem("mgS_loop", k_mg_loop<double, true>, mg_grid(H, n, k_mg_loop<double, true>, sm),
-                               blk, sm, H.g, C, run, (const double*)H.dSc, (double*)x, (double*)r,
+            R.launch_coop_smem("mgS_loop", k_mg_loop<double, true>, mg_grid(H, n, k_mg_loop<double, true>, sm, ntSd),
+                               dim3(ntSd), sm, H.g, C, run, (const double*)H.dSc, (double*)x, (double*)r,
                                (double*)p, (double*)q, M.r32, H.dctl, st, H.partials, gate);
         else
-            R.launch_coop_smem("mgA_loop", k_mg_loop<double, false>, mg_grid(H, n, k_mg_loop<double, false>, sm),
-                               blk, sm, H.g, C, run, (const double*)nullptr, (double*)x, (double*)r,
+            R.launch_coop_smem("mgA_loop", k_mg_loop<double, false>, mg_grid(H, n, k_mg_loop<double, false>, sm, ntAd),
+                               dim3(ntAd), sm, H.g, C, run, (const double*)nullptr, (double*)x, (double*)r,
                                (double*)p, (double*)q, M.r32, H.dctl, st, H.partials, gate);
     } else {
         // FP32 CG: the cycle reads the residual itself (its level-0 descriptor points at r32,
         // which the kernel does not touch)
         if (simple)
-            R.launch_coop_smem("mgS_loop_f32", k_mg_loop<float, true>, mg_grid(H, n, k_mg_loop<float, true>, sm),
-                               blk, sm, H.g, C, run, (const float*)nullptr, (float*)x, (float*)r,
+            R.launch_coop_smem("mgS_loop_f32", k_mg_loop<float, true>, mg_grid(H, n, k_mg_loop<float, true>, sm, ntSf),
+                               dim3(ntSf), sm, H.g, C, run, (const float*)nullptr, (float*)x, (float*)r,
                                (float*)p, (float*)q, (float*)r, H.dctl, st, H.partials, gate);
         else
-            R.launch_coop_smem("mgA_loop_f32", k_mg_loop<float, false>, mg_grid(H, n, k_mg_loop<float, false>, sm),
-                               blk, sm, H.g, C, run, (const float*)nullptr, (float*)x, (float*)r,
+            R.launch_coop_smem("mgA_loop_f32", k_mg_loop<float, false>, mg_grid(H, n, k_mg_loop<float, false>, sm, ntAf),
+                               dim3(ntAf), sm, H.g, C, run, (const float*)nullptr, (float*)x, (float*)r,
                                (float*)p, (float*)q, (float*)r, H.dctl, st, H.partials, gate);
     }
 }
