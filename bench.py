@@ -119,8 +119,8 @@ def kernel_model(name, nu, npf, d, loop_iters=20, mg=None):
 # `bench.py --kernels-only --steps 1`, profiles/kernel_traffic_spheres128.md) for the kernel
 # sources whose SHA-256 is given; reported as null once the sources differ.
 NCU_TRAFFIC = {
-    "sources_sha256": "06aa1e0ea591e6e198be929ce73cfacc906e4ec43ee6db524c2c8082abdb3611",
-    "bytes": {"cgA_dir": 38442752, "cgA_matvec": 74835712, "cgA_update": 74826496, "cgS_dir": 20134656, "cgS_matvec": 36942336, "cgS_update": 33583616, "cgA_dir_f32": 20354048, "cgA_matvec_f32": 65732352, "cgA_update_f32": 38471168, "cgS_dir_f32": 10069504, "cgS_matvec_f32": 26888192, "cgS_update_f32": 16808960, "cgA_loop": 2074676992, "cgS_loop": 61906944, "cgA_loop_f32": 567348992, "cgS_loop_f32": 36978944, "mgA_loop": 9430959104, "mgS_loop": 1215778304, "mgA_loop_f32": 6353433856, "mgS_loop_f32": 268300032},
+    "sources_sha256": "ed8ae25e059ae1c36a5698506cb8bedb113dd5e8a226bd04148b81ef3b66c36e",
+    "bytes": {"cgA_dir": 38441984, "cgA_matvec": 74849280, "cgA_update": 74820096, "cgS_dir": 20134400, "cgS_matvec": 36928512, "cgS_update": 33583360, "cgA_dir_f32": 20354816, "cgA_matvec_f32": 65718784, "cgA_update_f32": 38471424, "cgS_dir_f32": 10070272, "cgS_matvec_f32": 26864896, "cgS_update_f32": 16813312, "cgA_loop": 2075666944, "cgS_loop": 61878272, "cgA_loop_f32": 568718080, "cgS_loop_f32": 37058560, "mgA_loop": 8775379712, "mgS_loop": 336914688, "mgA_loop_f32": 5670449664, "mgS_loop_f32": 63746304},
 }
 
 
