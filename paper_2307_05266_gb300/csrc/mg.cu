@@ -31,8 +31,11 @@
 //   in block 0 alone, in its shared memory (the tables are copied there once per launch),
 //   with block barriers, while the other blocks wait at one grid barrier.  Every grid wait
 //   is bounded (grid_barrier).
+#include <algorithm>
+#include <atomic>
 #include <cstddef>
 #include <cstring>
+#include <thread>
 #include <type_traits>
 
 #include "cg_dev.cuh"
@@ -618,6 +621,36 @@ __global__ void __launch_bounds__(MgBlock<T, kS>::v, 1) k_mg_loop(Dev g, Compact
 
 namespace {
 
+// Host threads of the hierarchy build.  Every parallel step writes disjoint entries, and each
+// coarse sum keeps the serial order of its terms, so the hierarchy does not depend on the
+// thread count.
+int host_threads() {
+    const unsigned hw = std::thread::hardware_concurrency();
+    return (int)std::max(1u, std::min(hw ? hw : 1u, 16u));
+}
+
+// fn(t, begin, end) for the ranges [cut[t], cut[t + 1]), one thread each (the last on the
+// calling thread).
+template <class Fn>
+void run_ranges(const std::vector<long long>& cut, Fn fn) {
+    const int nt = (int)cut.size() - 1;
+    std::vector<std::thread> th;
+    for (int t = 0; t + 1 < nt; ++t) th.emplace_back(fn, t, cut[t], cut[t + 1]);
+    if (nt > 0) fn(nt - 1, cut[nt - 1], cut[nt]);
+    for (auto& x : th) x.join();
+}
+
+// nt equal ranges of [0, n).
+std::vector<long long> cuts(long long n, int nt) {
+    nt = (int)std::max(1ll, std::min<long long>(nt, n));
+    std::vector<long long> cut((size_t)nt + 1);
+    for (int t = 0; t <= nt; ++t) cut[t] = n * t / nt;
+    return cut;
+}
+
+// Equal ranges of [0, n) for the host threads (a single range below 2^16 entries).
+std::vector<long long> even_cuts(long long n) { return cuts(n, n < (1 << 16) ? 1 : host_threads()); }
+
 // One level on the host: coordinates (component a, voxel x, y, z of the level's grid), the
 // 7-point couplings and the diagonal with its mass.  The fine level keeps the device's own
 // neighbour table (row stride ld, sentinel n) and derives its coefficients: -1 per unknown
@@ -693,19 +726,21 @@ cudaError_t fine_level(const Handle& H, bool simple, HostLevel& L) {
     L.y.resize(n);
     L.z.resize(n);
     const long long plane = (long long)g.nx * g.ny;
-    for (long long k = 0; k < n; ++k) {
-        long long i = idx[k];
-        int a = 0;
-        if (!simple) {
-            a = (int)(i / g.stride);
-            i -= (long long)a * g.stride;
+    run_ranges(even_cuts(n), [&](int, long long k0, long long k1) {
+        for (long long k = k0; k < k1; ++k) {
+            long long i = idx[k];
+            int a = 0;
+            if (!simple) {
+                a = (int)(i / g.stride);
+                i -= (long long)a * g.stride;
+            }
+            const long long zz = i / plane, rem = i - zz * plane;
+            L.a[k] = (int8_t)a;
+            L.z[k] = (int16_t)zz;
+            L.y[k] = (int16_t)(rem / g.nx);
+            L.x[k] = (int16_t)(rem - (rem / g.nx) * g.nx);
         }
-        const long long zz = i / plane, rem = i - zz * plane;
-        L.a[k] = (int8_t)a;
-        L.z[k] = (int16_t)zz;
-        L.y[k] = (int16_t)(rem / g.nx);
-        L.x[k] = (int16_t)(rem - (rem / g.nx) * g.nx);
-    }
+    });
     if (!simple) {
         std::vector<uint8_t> ufl;
         if ((e = download(H.stream, H.ufl, (size_t)n, ufl)) != cudaSuccess) return e;
@@ -733,72 +768,114 @@ bool coarsen(const HostLevel& F, const int per[3], int ncomp, HostLevel& C,
     auto key = [&](int a, int X, int Y, int Z) {
         return ((long long)a * cz + Z) * cy * cx + (long long)Y * cx + X;
     };
-    for (long long i = 0; i < F.n; ++i) idx[key(F.a[i], F.x[i] >> 1, F.y[i] >> 1, F.z[i] >> 1)] = 0;
-    long long nc = 0;
+    // F is ordered by (a, z, y, x), so the entries of one coarse slab (a, z / 2) are
+    // contiguous: ranges cut at slab boundaries own disjoint sets of aggregates
+    std::vector<long long> cut = even_cuts(F.n);
+    for (size_t t = 1; t + 1 < cut.size(); ++t) {
+        long long i = std::max(cut[t], cut[t - 1]);
+        while (i > 0 && i < F.n && F.a[i] == F.a[i - 1] && (F.z[i] >> 1) == (F.z[i - 1] >> 1)) ++i;
+        cut[t] = i;
+    }
+    run_ranges(cut, [&](int, long long i0, long long i1) {
+        for (long long i = i0; i < i1; ++i) idx[key(F.a[i], F.x[i] >> 1, F.y[i] >> 1, F.z[i] >> 1)] = 0;
+    });
+    // coarse entries in (a, Z, Y, X) order: counts per slab, their prefix sums, numbering
+    const long long nslab = (long long)ncomp * cz, slab = (long long)cx * cy;
+    std::vector<long long> cnt((size_t)nslab + 1, 0);
+    const std::vector<long long> scut = cuts(nslab, nslab * slab < (1 << 16) ? 1 : host_threads());
+    run_ranges(scut, [&](int, long long s0, long long s1) {
+        for (long long sl = s0; sl < s1; ++sl) {
+            long long c = 0;
+            for (long long k = sl * slab; k < (sl + 1) * slab; ++k) c += idx[k] >= 0;
+            cnt[sl + 1] = c;
+        }
+    });
+    for (long long sl = 0; sl < nslab; ++sl) cnt[sl + 1] += cnt[sl];
+    const long long nc = cnt[nslab];
     C = HostLevel();
     C.dims[0] = cx;
     C.dims[1] = cy;
     C.dims[2] = cz;
-    for (int a = 0; a < ncomp; ++a)
-        for (int Z = 0; Z < cz; ++Z)
+    C.n = nc;
+    C.a.resize(nc);
+    C.x.resize(nc);
+    C.y.resize(nc);
+    C.z.resize(nc);
+    run_ranges(scut, [&](int, long long s0, long long s1) {
+        for (long long sl = s0; sl < s1; ++sl) {
+            long long v = cnt[sl];
+            const int a = (int)(sl / cz), Z = (int)(sl % cz);
             for (int Y = 0; Y < cy; ++Y)
                 for (int X = 0; X < cx; ++X) {
-                    int32_t& v = idx[key(a, X, Y, Z)];
-                    if (v < 0) continue;
-                    v = (int32_t)nc++;
-                    C.a.push_back((int8_t)a);
-                    C.x.push_back((int16_t)X);
-                    C.y.push_back((int16_t)Y);
-                    C.z.push_back((int16_t)Z);
+                    int32_t& e = idx[key(a, X, Y, Z)];
+                    if (e < 0) continue;
+                    e = (int32_t)v;
+                    C.a[v] = (int8_t)a;
+                    C.x[v] = (int16_t)X;
+                    C.y[v] = (int16_t)Y;
+                    C.z[v] = (int16_t)Z;
+                    ++v;
                 }
-    C.n = nc;
+        }
+    });
     C.ld = round_up(nc + 1, 32);
     agg.assign((size_t)F.n + 1, (uint32_t)nc);
     ch.assign((size_t)(8 * C.ld), (uint32_t)F.n);
-    for (long long i = 0; i < F.n; ++i) {
-        const uint32_t I = (uint32_t)idx[key(F.a[i], F.x[i] >> 1, F.y[i] >> 1, F.z[i] >> 1)];
-        agg[i] = I;
-        const int slot = (F.x[i] & 1) | ((F.y[i] & 1) << 1) | ((F.z[i] & 1) << 2);
-        ch[slot * C.ld + I] = (uint32_t)i;
-    }
+    run_ranges(cut, [&](int, long long i0, long long i1) {
+        for (long long i = i0; i < i1; ++i) {
+            const uint32_t I = (uint32_t)idx[key(F.a[i], F.x[i] >> 1, F.y[i] >> 1, F.z[i] >> 1)];
+            agg[i] = I;
+            const int slot = (F.x[i] & 1) | ((F.y[i] & 1) << 1) | ((F.z[i] & 1) << 2);
+            ch[slot * C.ld + I] = (uint32_t)i;
+        }
+    });
     // coarse neighbours: the aggregate one step away along each direction (wrapped on a
     // periodic axis); a step that wraps onto the aggregate itself is a diagonal coupling
     const int cd[3] = {cx, cy, cz};
     C.nb.assign((size_t)(6 * C.ld), (uint32_t)nc);
-    for (long long I = 0; I < nc; ++I)
-        for (int e = 0; e < 6; ++e) {
-            const int b = e >> 1, sgn = (e & 1) ? 1 : -1;
-            int c3[3] = {C.x[I], C.y[I], C.z[I]};
-            c3[b] += sgn;
-            if (c3[b] < 0 || c3[b] >= cd[b]) {
-                if (!per[b]) continue;
-                c3[b] = (c3[b] + cd[b]) % cd[b];
+    run_ranges(even_cuts(nc), [&](int, long long I0, long long I1) {
+        for (long long I = I0; I < I1; ++I)
+            for (int e = 0; e < 6; ++e) {
+                const int b = e >> 1, sgn = (e & 1) ? 1 : -1;
+                int c3[3] = {C.x[I], C.y[I], C.z[I]};
+                c3[b] += sgn;
+                if (c3[b] < 0 || c3[b] >= cd[b]) {
+                    if (!per[b]) continue;
+                    c3[b] = (c3[b] + cd[b]) % cd[b];
+                }
+                const int32_t J = idx[key(C.a[I], c3[0], c3[1], c3[2])];
+                if (J >= 0 && J != I) C.nb[e * C.ld + I] = (uint32_t)J;
             }
-            const int32_t J = idx[key(C.a[I], c3[0], c3[1], c3[2])];
-            if (J >= 0 && J != I) C.nb[e * C.ld + I] = (uint32_t)J;
-        }
-    // Galerkin coefficients, summed over the fine entries in their order
+    });
+    // Galerkin coefficients, each summed over its fine entries in their order (the slab
+    // ranges own their aggregates)
     C.w.assign((size_t)(6 * C.ld), 0.0);
     C.dg.assign((size_t)nc, 0.0);
     C.mass.assign((size_t)nc, 0.0);
-    for (long long i = 0; i < F.n; ++i) {
-        const uint32_t I = agg[i];
-        C.dg[I] += F.dg[i];
-        C.mass[I] += F.mass[i];
-        for (int e = 0; e < 6; ++e) {
-            const uint32_t j = F.nb[e * F.ld + i];
-            if (j >= (uint32_t)F.n) continue;
-            const double c = F.coef(e, i);
-            const uint32_t J = agg[j];
-            if (J == I) {
-                C.dg[I] += c;
-            } else {
-                if (C.nb[e * C.ld + I] != J) return false;
-                C.w[e * C.ld + I] += c;
+    std::atomic<bool> consistent(true);
+    run_ranges(cut, [&](int, long long i0, long long i1) {
+        for (long long i = i0; i < i1; ++i) {
+            const uint32_t I = agg[i];
+            C.dg[I] += F.dg[i];
+            C.mass[I] += F.mass[i];
+            for (int e = 0; e < 6; ++e) {
+                const uint32_t j = F.nb[e * F.ld + i];
+                if (j >= (uint32_t)F.n) continue;
+                const double c = F.coef(e, i);
+                const uint32_t J = agg[j];
+                if (J == I) {
+                    C.dg[I] += c;
+                } else {
+                    if (C.nb[e * C.ld + I] != J) {
+                        consistent = false;
+                        return;
+                    }
+                    C.w[e * C.ld + I] += c;
+                }
             }
         }
-    }
-    return true;
+    });
+    return consistent;
 }
 
 bool single_cell(const HostLevel& L) {
