@@ -119,8 +119,8 @@ def kernel_model(name, nu, npf, d, loop_iters=20, mg=None):
 # `bench.py --kernels-only --steps 1`, profiles/kernel_traffic_spheres128.md) for the kernel
 # sources whose SHA-256 is given; reported as null once the sources differ.
 NCU_TRAFFIC = {
-    "sources_sha256": "ed8ae25e059ae1c36a5698506cb8bedb113dd5e8a226bd04148b81ef3b66c36e",
-    "bytes": {"cgA_dir": 38441984, "cgA_matvec": 74849280, "cgA_update": 74820096, "cgS_dir": 20134400, "cgS_matvec": 36928512, "cgS_update": 33583360, "cgA_dir_f32": 20354816, "cgA_matvec_f32": 65718784, "cgA_update_f32": 38471424, "cgS_dir_f32": 10070272, "cgS_matvec_f32": 26864896, "cgS_update_f32": 16813312, "cgA_loop": 2075666944, "cgS_loop": 61878272, "cgA_loop_f32": 568718080, "cgS_loop_f32": 37058560, "mgA_loop": 8775379712, "mgS_loop": 336914688, "mgA_loop_f32": 5670449664, "mgS_loop_f32": 63746304},
+    "sources_sha256": "e6aa2003969d23e0ee7027561faf301861125d9b6589a5844133cb7eeb5f2f52",
+    "bytes": {"cgA_dir": 38450944, "cgA_matvec": 74894592, "cgA_update": 74832384, "cgS_dir": 20134400, "cgS_matvec": 36928256, "cgS_update": 33585664, "cgA_dir_f32": 20354560, "cgA_matvec_f32": 65753344, "cgA_update_f32": 38481664, "cgS_dir_f32": 10069248, "cgS_matvec_f32": 26866688, "cgS_update_f32": 16811520, "cgA_loop": 2085093888, "cgS_loop": 61874688, "cgA_loop_f32": 562364416, "cgS_loop_f32": 37092352, "mgA_loop": 8787909120, "mgS_loop": 338504960, "mgA_loop_f32": 5679827712, "mgS_loop_f32": 61202688},
 }
 
 
