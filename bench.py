@@ -119,8 +119,8 @@ def kernel_model(name, nu, npf, d, loop_iters=20, mg=None):
 # `bench.py --kernels-only --steps 1`, profiles/kernel_traffic_spheres128.md) for the kernel
 # sources whose SHA-256 is given; reported as null once the sources differ.
 NCU_TRAFFIC = {
-    "sources_sha256": "e6aa2003969d23e0ee7027561faf301861125d9b6589a5844133cb7eeb5f2f52",
-    "bytes": {"cgA_dir": 38450944, "cgA_matvec": 74894592, "cgA_update": 74832384, "cgS_dir": 20134400, "cgS_matvec": 36928256, "cgS_update": 33585664, "cgA_dir_f32": 20354560, "cgA_matvec_f32": 65753344, "cgA_update_f32": 38481664, "cgS_dir_f32": 10069248, "cgS_matvec_f32": 26866688, "cgS_update_f32": 16811520, "cgA_loop": 2085093888, "cgS_loop": 61874688, "cgA_loop_f32": 562364416, "cgS_loop_f32": 37092352, "mgA_loop": 8787909120, "mgS_loop": 338504960, "mgA_loop_f32": 5679827712, "mgS_loop_f32": 61202688},
+    "sources_sha256": "4ed8817b95f76add0d8073190d714b1f63e052c5c12a44f04d6d0fa8366a7d0f",
+    "bytes": {"cgA_dir": 38443264, "cgA_matvec": 74947328, "cgA_update": 74824448, "cgS_dir": 20134144, "cgS_matvec": 36927744, "cgS_update": 33583360, "cgA_dir_f32": 20354560, "cgA_matvec_f32": 65739776, "cgA_update_f32": 38472448, "cgS_dir_f32": 10069504, "cgS_matvec_f32": 26864640, "cgS_update_f32": 16809472, "cgA_loop": 2074717696, "cgS_loop": 61835264, "cgA_loop_f32": 571134208, "cgS_loop_f32": 37000448, "mgA_loop": 8774293760, "mgS_loop": 336570112, "mgA_loop_f32": 5670988800, "mgS_loop_f32": 63671808},
 }
 
 

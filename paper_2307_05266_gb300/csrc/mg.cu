@@ -630,13 +630,19 @@ int host_threads() {
 }
 
 // fn(t, begin, end) for the ranges [cut[t], cut[t + 1]), one thread each (the last on the
-// calling thread).
+// calling thread).  When a thread cannot be had, the ranges left run on the calling thread:
+// no exception leaves the library.  fn itself allocates nothing.
 template <class Fn>
 void run_ranges(const std::vector<long long>& cut, Fn fn) {
     const int nt = (int)cut.size() - 1;
     std::vector<std::thread> th;
-    for (int t = 0; t + 1 < nt; ++t) th.emplace_back(fn, t, cut[t], cut[t + 1]);
-    if (nt > 0) fn(nt - 1, cut[nt - 1], cut[nt]);
+    int t = 0;
+    try {
+        th.reserve((size_t)std::max(nt - 1, 0));
+        for (; t + 1 < nt; ++t) th.emplace_back(fn, t, cut[t], cut[t + 1]);
+    } catch (...) {
+    }
+    for (; t < nt; ++t) fn(t, cut[t], cut[t + 1]);
     for (auto& x : th) x.join();
 }
 
